@@ -1,0 +1,169 @@
+"""Problem descriptions of the paper's workloads, as plain parameter dicts.
+
+A problem description is a dict of parameter VALUES in the paper's notation
+(lattice, EOS parameters a, b, R, omega, T_r, interaction strengths g_kk',
+mixing weight A_kk, relaxation times, wetting phi / drho, boundary kinds). Both
+the CUDA binding and the oracle binding translate it with their own code.
+
+Keys:
+  lattice      "D2Q9" | "D3Q19"
+  shape        (nx, ny, nz), nz = 1 for D2Q9
+  ncomp        1 | 2
+  real         "f32" | "f64" (storage and compute type of the CUDA path)
+  collision    "BGK" | "MRT"
+  velocity     "component" (u^k = j^k / rho^k) | "common" (Shan-Chen common velocity)
+  tau          [tau_1, tau_2]
+  mrt_rates    per component, 19 rates in the moment order of the MRT basis
+               (stress rates are replaced by 1/tau, conserved rates by 0)
+  psi          per component "eos" | "rho" | "exp"
+  eos          per component "CS" | "PR" | "VdW" | "RK" | "RKS"
+  eos_a, eos_b, eos_R, eos_omega, T_red, alpha, A   per component
+  g            2x2 interaction strengths
+  wet_phi, wet_drho, rho_lo, rho_hi                per component
+  accel        per component body acceleration (3)
+  bc           6 faces (-x, +x, -y, +y, -z, +z): "periodic" | "wall" | "pressure"
+  bc_rho       6 x ncomp face densities (pressure faces)
+"""
+import numpy as np
+
+from . import droplet_field, grf_porous_medium, random_droplets
+
+# Non-hydrodynamic MRT relaxation rates. D2Q9 after Lallemand & Luo (2000):
+# s_e = 1.64, s_eps = 1.54, s_q = 1.9. D3Q19 after d'Humieres et al. (2002):
+# s_e = 1.19, s_eps = 1.4, s_q = 1.2, s_pi = 1.4, s_m = 1.98.
+MRT_D2Q9 = [0.0, 1.64, 1.54, 0.0, 1.9, 0.0, 1.9, 1.0, 1.0] + [0.0] * 10
+MRT_D3Q19 = [0.0, 1.19, 1.4, 0.0, 1.2, 0.0, 1.2, 0.0, 1.2, 1.0, 1.4, 1.0, 1.4, 1.0, 1.0,
+             1.0, 1.98, 1.98, 1.98]
+
+# EOS parameter sets of the paper's thermodynamic-consistency runs (Yuan & Schaefer 2006):
+EOS_PARAMS = {
+    "CS": dict(eos_a=1.0, eos_b=4.0, eos_R=1.0, eos_omega=0.0),
+    "PR": dict(eos_a=2.0 / 49.0, eos_b=2.0 / 21.0, eos_R=1.0, eos_omega=0.344),
+    "RK": dict(eos_a=2.0 / 49.0, eos_b=2.0 / 21.0, eos_R=1.0, eos_omega=0.0),
+    "RKS": dict(eos_a=2.0 / 49.0, eos_b=2.0 / 21.0, eos_R=1.0, eos_omega=0.344),
+    "VdW": dict(eos_a=9.0 / 49.0, eos_b=2.0 / 21.0, eos_R=1.0, eos_omega=0.0),
+}
+
+# Liquid / vapour densities used to shape initial droplets (Maxwell construction of
+# the EOS at the stated reduced temperature; only the initial condition uses them).
+COEX = {
+    ("CS", 0.7): (0.00929415, 0.358131),     # a = 0.5, b = 4 (coexistence is independent of a)
+    ("PR", 0.6): (0.0102274, 8.72493),       # a = 2/49, b = 2/21, omega = 0.344
+    ("PR", 0.8): (0.197079, 7.20405),
+    ("CS", 0.8): (0.0217232, 0.307196),
+    ("VdW", 0.8): (0.838834, 6.76447),
+}
+
+# Zhang-Chen / Shan-Chen mixing weight A_kk that satisfies mechanical stability
+# (flat-interface coexistence equal to the Maxwell pair within 0.1 %), found by
+# bisection on the vapour density of a flat liquid slab (D2Q9, BGK, tau = 1).
+A_STAR = {("CS", 0.7): -0.276, ("CS", 0.8): -0.275, ("PR", 0.6): -0.233, ("PR", 0.8): -0.249}
+
+# psi = exp(-1/rho) with g = -10/3: coexistence 0.367528 / 2.78279, ratio 7.57,
+# the ratio of about 7.6 of the paper's performance droplet (Section 5)
+EXP_G = -10.0 / 3.0
+EXP_COEX = (0.367528, 2.78279)
+
+
+def base_case(lattice, shape, **kw):
+    case = dict(lattice=lattice, shape=tuple(shape), ncomp=1, real="f32", collision="BGK",
+                velocity="component", tau=[1.0, 1.0],
+                mrt_rates=[MRT_D2Q9 if lattice == "D2Q9" else MRT_D3Q19] * 2,
+                psi=["eos", "eos"], eos=["CS", "CS"], T_red=[0.7, 0.7], alpha=[1.0, 1.0],
+                A=[0.0, 0.0], g=[[-1.0, 0.0], [0.0, -1.0]], wet_phi=[1.0, 1.0],
+                wet_drho=[0.0, 0.0], rho_lo=[0.0, 0.0], rho_hi=[1e30, 1e30],
+                accel=[[0.0, 0.0, 0.0], [0.0, 0.0, 0.0]], bc=["periodic"] * 6,
+                bc_rho=[[0.0, 0.0]] * 6)
+    case.update(kw)
+    return case
+
+
+def with_eos(case, name, T_red, comps=(0,)):
+    """Set the EOS (and its paper parameter set) of the given components."""
+    c = dict(case)
+    for key in ("eos_a", "eos_b", "eos_R", "eos_omega"):
+        v = list(c.get(key, [0.0, 0.0]))
+        v = v + [v[-1]] * (2 - len(v))
+        for k in comps:
+            v[k] = EOS_PARAMS[name][key]
+        c[key] = v
+    eos = list(c.get("eos", ["CS", "CS"]))
+    tr = list(c.get("T_red", [0.7, 0.7]))
+    psi = list(c.get("psi", ["eos", "eos"]))
+    for k in comps:
+        eos[k] = name
+        tr[k] = T_red
+        psi[k] = "eos"
+    c.update(eos=eos, T_red=tr, psi=psi)
+    return c
+
+
+# ---------------------------------------------------------------------------
+# Workloads
+# ---------------------------------------------------------------------------
+
+def droplet_2d_cs(n=128, radius=25.0, width=5.0, real="f64"):
+    """D2Q9 single-component Shan-Chen, Carnahan-Starling (a = 0.5, b = 4, R = 1,
+    T = 0.7 Tc), BGK tau = 1, n x n periodic, one droplet of radius 25 with a
+    tanh interface of width 5 at the centre."""
+    A = A_STAR[("CS", 0.7)]
+    case = base_case("D2Q9", (n, n, 1), real=real, A=[A, A])
+    case = with_eos(case, "CS", 0.7)
+    case["eos_a"] = [0.5, 0.5]
+    rg, rl = COEX[("CS", 0.7)]
+    rho = droplet_field((n, n, 1), [(n / 2.0, n / 2.0)], [radius], rl, rg, width)
+    return case, dict(rho=[rho])
+
+
+def droplets_3d_pr(n=256, count=8, rmin=12.0, rmax=40.0, width=5.0, seed=1234, real="f32",
+                   shape=None, A=A_STAR[("PR", 0.6)]):
+    """D3Q19 single-component Shan-Chen, Peng-Robinson (a = 2/49, b = 2/21, R = 1,
+    omega = 0.344, T = 0.6 Tc), MRT, periodic cube, `count` droplets with seeded
+    radii U[rmin, rmax] at random non-overlapping centres."""
+    shape = tuple(shape) if shape is not None else (n, n, n)
+    case = base_case("D3Q19", shape, real=real, collision="MRT", A=[A, A])
+    case = with_eos(case, "PR", 0.6)
+    rg, rl = COEX[("PR", 0.6)]
+    centers, radii = random_droplets(shape, count, rmin, rmax, width, seed)
+    rho = droplet_field(shape, centers, radii, rl, rg, width)
+    return case, dict(rho=[rho], centers=centers, radii=radii)
+
+
+def droplet_3d_exp(n=256, radius=30.0, width=5.0, real="f32", shape=None):
+    """The paper's performance case: D3Q19 BGK, psi = exp(-1/rho), one droplet of
+    radius 30 in its vapour, periodic."""
+    shape = tuple(shape) if shape is not None else (n, n, n)
+    case = base_case("D3Q19", shape, real=real, psi=["exp", "exp"],
+                     g=[[EXP_G, 0.0], [0.0, EXP_G]])
+    rg, rl = EXP_COEX
+    c = [s / 2.0 for s in shape]
+    rho = droplet_field(shape, [c], [radius], rl, rg, width)
+    return case, dict(rho=[rho])
+
+
+def porous_two_component(shape=(400, 400, 400), porosity=0.15, corr_length=6.0, seed=7,
+                         buffer=8, real="f32", theta_phi=1.2, rho_major=1.0,
+                         rho_minor=0.03, g12=0.19, gkk=-0.009, tau_w=1.0, tau_nw=0.55,
+                         drho_in=0.02):
+    """D3Q19 two-component Shan-Chen (psi = rho, A = 0) in a Gaussian-random-field
+    porous medium (porosity 0.15, correlation length 6) with 8-lu fluid buffers.
+    Component 0 = wetting phase initially saturating the domain, component 1 =
+    non-wetting phase injected at x = 0 through a constant-density face against
+    a constant-density outlet. Viscosity ratio mu_nw : mu_w = 1 : 10 for
+    tau_nw = 0.55, tau_w = 1.0."""
+    nx, ny, nz = shape
+    solid, used_seed = grf_porous_medium(shape, porosity, corr_length, seed, buffer=buffer)
+    case = base_case("D3Q19", shape, real=real, ncomp=2, psi=["rho", "rho"],
+                     g=[[gkk, g12], [g12, gkk]], tau=[tau_w, tau_nw],
+                     wet_phi=[theta_phi, 1.0], wet_drho=[0.0, 0.0],
+                     rho_lo=[0.0, 0.0], rho_hi=[rho_major * 1.5, rho_major * 1.5],
+                     bc=["pressure", "pressure", "periodic", "periodic", "periodic", "periodic"])
+    bc_rho = [[0.0, 0.0] for _ in range(6)]
+    bc_rho[0] = [rho_minor, rho_major + drho_in]   # inlet: non-wetting phase
+    bc_rho[1] = [rho_major, rho_minor]             # outlet: wetting phase
+    case["bc_rho"] = bc_rho
+    rho_w = np.full((nz, ny, nx), rho_major)
+    rho_nw = np.full((nz, ny, nx), rho_minor)
+    rho_w[:, :, :buffer] = rho_minor
+    rho_nw[:, :, :buffer] = rho_major
+    return case, dict(rho=[rho_w, rho_nw], solid=solid, seed=used_seed)

@@ -1,0 +1,370 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks one part of the oracle against something other than the
+oracle itself: a value printed in the paper, a closed form, an exact invariant
+or a special case that reduces to a textbook formula.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import cases, droplet_field, random_field, random_solids
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _table():
+    with open(os.path.join(GOLD, "coex_dens_table.json")) as fh:
+        return json.load(fh)
+
+
+# ---------------------------------------------------------------------------
+# EOS and Maxwell construction (Section 3.1-3.2, Table coex_dens; Section 4)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("eos", ["CS", "PR", "RK", "RKS", "VdW"])
+def test_maxwell_matches_table_coex_dens(eos):
+    t = _table()
+    p = cases.EOS_PARAMS[eos]
+    rg, rl, _ = oracle.maxwell(eos, p["eos_a"], p["eos_b"], p["eos_R"], p["eos_omega"], t["T_red"])
+    g4, l4 = t["maxwell_4dp"][eos]
+    # the table truncates to 4 decimals: printed <= exact < printed + 1e-4
+    assert g4 - 1e-12 <= rg < g4 + 1e-4, (eos, rg, g4)
+    assert l4 - 1e-12 <= rl < l4 + 1e-4, (eos, rl, l4)
+
+
+def test_maxwell_vdw_six_digits():
+    t = _table()["vdw_section4_6sig"]
+    p = cases.EOS_PARAMS["VdW"]
+    rg, rl, _ = oracle.maxwell("VdW", p["eos_a"], p["eos_b"], 1.0, 0.0, 0.8)
+    assert abs(rg - t["rho_g"]) < 5e-7
+    assert abs(rl - t["rho_l"]) < 5e-6
+
+
+def test_critical_temperature_closed_forms():
+    # van der Waals: Tc = 8a/(27 b R); Redlich-Kwong-Soave: Tc = Omega_b a / (Omega_a b R)
+    # with Omega_a = 1/(9 (2^(1/3) - 1)), Omega_b = (2^(1/3) - 1)/3 (exact RK constants)
+    a, b = 9 / 49, 2 / 21
+    assert abs(oracle.eos_Tc("VdW", a, b, 1.0) - 8 * a / (27 * b)) < 1e-9
+    om_a = 1.0 / (9.0 * (2 ** (1 / 3) - 1.0))
+    om_b = (2 ** (1 / 3) - 1.0) / 3.0
+    a, b = 2 / 49, 2 / 21
+    assert abs(oracle.eos_Tc("RKS", a, b, 1.0) / (om_b * a / (om_a * b)) - 1) < 1e-8
+    assert abs(oracle.eos_Tc("RK", a, b, 1.0) / (om_b * a / (om_a * b)) ** (2 / 3) - 1) < 1e-8
+
+
+def test_maxwell_equal_pressures_and_stored_initial_pairs():
+    for (eos, tr), (g0, l0) in cases.COEX.items():
+        p = dict(cases.EOS_PARAMS[eos])
+        if eos == "CS" and tr == 0.7:
+            p["eos_a"] = 0.5
+        rg, rl, ps = oracle.maxwell(eos, p["eos_a"], p["eos_b"], 1.0, p["eos_omega"], tr)
+        assert abs(rg / g0 - 1) < 2e-5 and abs(rl / l0 - 1) < 2e-5
+        pg = oracle.eos_pressure(eos, p["eos_a"], p["eos_b"], 1.0, p["eos_omega"], tr, rg)
+        pl = oracle.eos_pressure(eos, p["eos_a"], p["eos_b"], 1.0, p["eos_omega"], tr, rl)
+        assert abs(pg - ps) < 1e-10 * max(1.0, abs(ps)) and abs(pl - ps) < 1e-10 * max(1.0, abs(ps))
+
+
+def test_exp_pseudopotential_ratio_of_paper_performance_case():
+    # Section 5: psi = exp(-1/rho) droplet with a density ratio of about 7.6
+    case, _ = cases.droplet_3d_exp(shape=(4, 4, 4))
+    rg, rl, _ = oracle.maxwell_bulk(case, 0, 1e-3, 50.0)
+    assert abs(rl / rg - 7.6) < 0.1
+    assert abs(rg / cases.EXP_COEX[0] - 1) < 1e-5 and abs(rl / cases.EXP_COEX[1] - 1) < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# Lattice and collision (Section 2.1, Eqs. lbe, collision_model, macroeq, edm)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19"])
+def test_lattice_isotropy(lattice):
+    shape = (3, 3, 1) if lattice == "D2Q9" else (3, 3, 3)
+    s = oracle.OracleSim(cases.base_case(lattice, shape))
+    e, w = s.e.astype(float), s.w
+    d = 2 if lattice == "D2Q9" else 3
+    assert s.Q == (9 if d == 2 else 19)
+    assert abs(w.sum() - 1) < 1e-15
+    assert np.allclose(np.einsum("i,ia->a", w, e), 0, atol=1e-15)
+    assert np.allclose(np.einsum("i,ia,ib->ab", w, e, e)[:d, :d], np.eye(d) / 3, atol=1e-15)
+    assert np.allclose(np.einsum("i,ia,ib,ic->abc", w, e, e, e), 0, atol=1e-15)
+    T4 = np.einsum("i,ia,ib,ic,id->abcd", w, e, e, e, e)[:d, :d, :d, :d]
+    I = np.eye(d)
+    iso = (np.einsum("ab,cd->abcd", I, I) + np.einsum("ac,bd->abcd", I, I)
+           + np.einsum("ad,bc->abcd", I, I)) / 9.0
+    assert np.allclose(T4, iso, atol=1e-15)
+
+
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19"])
+def test_mrt_basis_orthogonal_and_inverse(lattice):
+    shape = (3, 3, 1) if lattice == "D2Q9" else (3, 3, 3)
+    s = oracle.OracleSim(cases.base_case(lattice, shape, collision="MRT"))
+    M, Mi = s.mrt_matrices()
+    assert np.allclose(M @ Mi, np.eye(s.Q), atol=1e-12)
+    G = M @ M.T
+    assert np.allclose(G - np.diag(np.diag(G)), 0, atol=1e-12)
+    # row 0 is the density, the momentum rows are the velocity components
+    assert np.allclose(M[0], 1)
+    assert np.allclose(M[3], s.e[:, 0]) and np.allclose(M[5], s.e[:, 1])
+    if lattice == "D3Q19":
+        assert np.allclose(M[7], s.e[:, 2])
+
+
+def _random_pops(s, seed, rho0=1.0):
+    f = s.w * rho0 * (1.0 + 0.2 * (np.random.default_rng(seed).random(s.Q) - 0.5))
+    return f
+
+
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19"])
+def test_bgk_tau_one_gives_shifted_equilibrium(lattice):
+    # special case: BGK with tau = 1 and EDM gives f* = f^eq(rho, u + F/rho); its
+    # moments are rho, rho u + F and rho c_s^2 I + rho u' u' (closed forms)
+    shape = (3, 3, 1) if lattice == "D2Q9" else (3, 3, 3)
+    s = oracle.OracleSim(cases.base_case(lattice, shape, tau=[1.0, 1.0]))
+    d = s.dim
+    f = _random_pops(s, 1, 1.3)
+    F = np.array([1e-3, -2e-3, 5e-4 if d == 3 else 0.0])
+    out = s.collide_single(f, F)
+    e = s.e.astype(float)
+    rho = f.sum()
+    j = f @ e
+    up = (j + F) / rho
+    assert abs(out.sum() - rho) < 1e-14
+    assert np.allclose(out @ e, j + F, atol=1e-15)
+    P = np.einsum("i,ia,ib->ab", out, e, e)[:d, :d]
+    assert np.allclose(P, rho / 3 * np.eye(d) + rho * np.outer(up, up)[:d, :d], atol=1e-14)
+
+
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19"])
+def test_mrt_with_equal_rates_is_bgk(lattice):
+    shape = (3, 3, 1) if lattice == "D2Q9" else (3, 3, 3)
+    tau = 0.8
+    bgk = oracle.OracleSim(cases.base_case(lattice, shape, tau=[tau, tau]))
+    mrt = oracle.OracleSim(cases.base_case(lattice, shape, tau=[tau, tau], collision="MRT",
+                                           mrt_rates=[[1 / tau] * 19] * 2))
+    f = _random_pops(bgk, 2)
+    F = np.array([2e-4, 1e-4, -3e-4])
+    assert np.allclose(bgk.collide_single(f, F), mrt.collide_single(f, F), atol=1e-15)
+
+
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19"])
+def test_mrt_conserves_mass_and_adds_force(lattice):
+    shape = (3, 3, 1) if lattice == "D2Q9" else (3, 3, 3)
+    s = oracle.OracleSim(cases.base_case(lattice, shape, collision="MRT", tau=[0.7, 0.7]))
+    f = _random_pops(s, 3, 2.0)
+    F = np.array([1e-3, 2e-3, -1e-3 if s.dim == 3 else 0.0])
+    out = s.collide_single(f, F)
+    e = s.e.astype(float)
+    assert abs(out.sum() - f.sum()) < 1e-14
+    assert np.allclose(out @ e, f @ e + F, atol=1e-15)
+    # the stress relaxes at 1/tau towards its equilibrium value (MRT stress moment)
+    rho, u = f.sum(), (f @ e) / f.sum()
+    up = u + F / rho
+    Pxy_in = np.sum(f * e[:, 0] * e[:, 1])
+    Pxy_out = np.sum(out * e[:, 0] * e[:, 1])
+    # post-collision: Pxy* = Pxy - (Pxy - rho ux uy)/tau + rho (ux' uy' - ux uy)
+    expect = Pxy_in - (Pxy_in - rho * u[0] * u[1]) / 0.7 + rho * (up[0] * up[1] - u[0] * u[1])
+    assert abs(Pxy_out - expect) < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# Interaction force (Eq. software_ff_force_mcmp) on polynomial fields
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19"])
+def test_sc_force_exact_on_quadratic_psi(lattice):
+    # With G_i = w_i / c_s^2 the stencil reproduces the gradient exactly for any
+    # quadratic field (odd lattice moments vanish), so F_SC = -g psi grad(psi).
+    shape = (12, 11, 1) if lattice == "D2Q9" else (9, 8, 7)
+    g = -1.3
+    s = oracle.OracleSim(cases.base_case(lattice, shape, psi=["rho"], g=[[g, 0], [0, g]]))
+    nz, ny, nx = s.shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    psi = 1.0 + 0.1 * x - 0.05 * y + 0.02 * x * y + 0.01 * y * y
+    grad = [0.1 + 0.02 * y, -0.05 + 0.02 * x + 0.02 * y, 0.0 * x]
+    if s.dim == 3:
+        psi = psi + 0.03 * z + 0.015 * x * z - 0.01 * z * z
+        grad[0] = grad[0] + 0.015 * z
+        grad[2] = 0.03 + 0.015 * x - 0.02 * z
+    F = s.interaction_force(psi[None], np.zeros((1,) + s.shape))[0]
+    inner = (slice(1, -1) if s.dim == 3 else slice(None), slice(1, -1), slice(1, -1))
+    for a in range(s.dim):
+        assert np.allclose(F[inner + (a,)], (-g * psi * grad[a])[inner], atol=1e-13)
+
+
+def test_zc_force_and_mixing_weight():
+    # F = A F_ZC + (1 - A) F_SC with F_ZC = -grad U exactly for quadratic U
+    shape = (9, 8, 7)
+    A = -0.3
+    s = oracle.OracleSim(cases.base_case("D3Q19", shape, psi=["rho"], A=[A, A], g=[[-1, 0], [0, -1]]))
+    nz, ny, nx = s.shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    U = 0.2 * x * x - 0.1 * y * z + 0.3 * z
+    psi = np.zeros_like(U)
+    F = s.interaction_force(psi[None], U[None])[0]
+    inner = (slice(1, -1), slice(1, -1), slice(1, -1))
+    gradU = [0.4 * x, -0.1 * z, -0.1 * y + 0.3]
+    for a in range(3):
+        assert np.allclose(F[inner + (a,)], (-A * gradU[a])[inner], atol=1e-13)
+
+
+def test_cross_component_force():
+    # two components: F^1 = -psi^1 (g11 grad psi^1 + g12 grad psi^2) for linear psi
+    shape = (8, 7, 6)
+    g = [[-0.7, 0.4], [0.4, -0.2]]
+    s = oracle.OracleSim(cases.base_case("D3Q19", shape, ncomp=2, psi=["rho", "rho"], g=g))
+    nz, ny, nx = s.shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    p1 = 1.0 + 0.1 * x + 0.2 * z
+    p2 = 0.5 - 0.05 * y + 0.1 * x
+    g1 = np.array([0.1, 0.0, 0.2])
+    g2 = np.array([0.1, -0.05, 0.0])
+    F = s.interaction_force(np.stack([p1, p2]), np.zeros((2,) + s.shape))
+    inner = (slice(1, -1), slice(1, -1), slice(1, -1))
+    for k, (pk, gk) in enumerate([(p1, None), (p2, None)]):
+        for a in range(3):
+            expect = -pk * (g[k][0] * g1[a] + g[k][1] * g2[a])
+            assert np.allclose(F[k][inner + (a,)], expect[inner], atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# Whole-step invariants (Eqs. lbe_steps, edm)
+# ---------------------------------------------------------------------------
+
+def test_mass_and_momentum_conserved_periodic_droplet():
+    case, init = cases.droplet_2d_cs(n=64, radius=14.0)
+    s = oracle.OracleSim(case)
+    s.init_fields(0, init["rho"][0])
+    m0, p0 = s.diagnostics()
+    s.step(400)
+    m1, p1 = s.diagnostics()
+    assert abs(m1[0] - m0[0]) < 1e-12 * m0[0]
+    assert np.abs(p1).max() < 1e-12 * m0[0]
+
+
+def test_mass_conserved_with_solids_mrt_two_components():
+    shape = (13, 11, 9)
+    case = cases.base_case("D3Q19", shape, ncomp=2, collision="MRT", psi=["rho", "rho"],
+                           g=[[-0.01, 0.15], [0.15, -0.01]], tau=[1.0, 0.7],
+                           wet_phi=[1.1, 1.0], rho_hi=[2.0, 2.0])
+    s = oracle.OracleSim(case)
+    s.set_geometry(random_solids(shape, 0.2, 11))
+    s.init_fields(0, random_field(shape, 0.8, 1.0, 12))
+    s.init_fields(1, random_field(shape, 0.05, 0.1, 13))
+    m0, _ = s.diagnostics()
+    s.step(100)
+    m1, _ = s.diagnostics()
+    assert np.allclose(m1, m0, rtol=1e-13)
+
+
+def test_body_force_momentum_growth():
+    # with periodic faces the interaction forces sum to zero, so the momentum
+    # sum_x (j + F/2) grows by a * (total mass) per step exactly
+    shape = (10, 9, 8)
+    a = np.array([1e-5, -2e-5, 3e-6])
+    case = cases.base_case("D3Q19", shape, psi=["exp"], g=[[cases.EXP_G, 0], [0, cases.EXP_G]],
+                           accel=[list(a), list(a)], collision="MRT")
+    s = oracle.OracleSim(case)
+    s.init_fields(0, random_field(shape, 0.5, 2.0, 21))
+    m0, p0 = s.diagnostics()
+    s.step(5)
+    m1, p1 = s.diagnostics()
+    assert np.allclose(p1[0] - p0[0], 5 * a * m0[0], rtol=1e-10, atol=1e-15)
+
+
+def test_translation_and_mirror_symmetry():
+    shape = (16, 12, 1)
+    case = cases.base_case("D2Q9", shape, collision="MRT", psi=["exp"],
+                           g=[[cases.EXP_G, 0], [0, cases.EXP_G]])
+    rho = random_field(shape, 0.5, 2.0, 31)
+    a = oracle.OracleSim(case)
+    a.init_fields(0, rho)
+    a.step(20)
+    ra, ua = a.macroscopic(0)
+    # translation by (3, 5)
+    b = oracle.OracleSim(case)
+    b.init_fields(0, np.roll(rho, (5, 3), axis=(1, 2)))
+    b.step(20)
+    rb, ub = b.macroscopic(0)
+    assert np.allclose(np.roll(ra, (5, 3), axis=(1, 2)), rb, atol=1e-13)
+    # mirror x -> -x: rho mirrored, u_x changes sign
+    c = oracle.OracleSim(case)
+    c.init_fields(0, rho[:, :, ::-1])
+    c.step(20)
+    rc, uc = c.macroscopic(0)
+    assert np.allclose(ra[:, :, ::-1], rc, atol=1e-13)
+    assert np.allclose(-ua[0][:, :, ::-1], uc[0], atol=1e-13)
+    assert np.allclose(ua[1][:, :, ::-1], uc[1], atol=1e-13)
+
+
+def test_rest_state_stays_at_rest():
+    # uniform density, no force: f = f^eq(rho, 0) is a fixed point of the step
+    shape = (6, 5, 4)
+    case = cases.base_case("D3Q19", shape, collision="MRT")
+    case = cases.with_eos(case, "PR", 0.6)
+    s = oracle.OracleSim(case)
+    s.init_fields(0, np.full(s.shape, 3.0))
+    f0 = s.populations(0)
+    s.step(3)
+    assert np.allclose(s.populations(0), f0, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# Wetting (Eq. improved_virtual_density)
+# ---------------------------------------------------------------------------
+
+def test_virtual_density_special_cases():
+    shape = (10, 8, 6)
+    solid = np.zeros((6, 8, 10), dtype=np.uint8)
+    solid[:, :, 4:6] = 1  # a slab of solid two layers thick
+    for phi, drho, expect in [(1.0, 0.0, 0.7), (1.3, 0.0, 0.91), (1.0, 0.2, 0.5), (3.0, 0.0, 1.5)]:
+        case = cases.base_case("D3Q19", shape, psi=["rho"], wet_phi=[phi, phi],
+                               wet_drho=[drho, drho], rho_lo=[0.1, 0.1], rho_hi=[1.5, 1.5])
+        s = oracle.OracleSim(case)
+        s.set_geometry(solid)
+        s.init_fields(0, np.full(s.shape, 0.7))
+        psi, rho = s.psi(0)
+        b = s.boundary_solids().astype(bool)
+        assert b.sum() == 2 * 6 * 8
+        assert np.allclose(rho[b], expect, atol=1e-14)   # includes the limiter (phi = 3)
+        assert np.allclose(psi[b], rho[b], atol=1e-14)   # psi = rho at solids too
+
+
+def test_neutral_wetting_flat_wall_force_vanishes_normal():
+    # phi = 1, drho = 0 on a uniform fluid: solids mirror the fluid density, so
+    # the interaction force at wall-adjacent fluid nodes vanishes (90 degrees)
+    shape = (8, 9, 1)
+    solid = np.zeros((1, 9, 8), dtype=np.uint8)
+    solid[:, 0, :] = 1
+    case = cases.base_case("D2Q9", shape, psi=["exp"], g=[[cases.EXP_G, 0], [0, cases.EXP_G]],
+                           bc=["periodic", "periodic", "wall", "wall", "periodic", "periodic"])
+    s = oracle.OracleSim(case)
+    s.set_geometry(solid)
+    s.init_fields(0, np.full(s.shape, 1.7))
+    F = s.force(0)
+    assert np.abs(F).max() < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# Constant-density faces
+# ---------------------------------------------------------------------------
+
+def test_pressure_faces_fix_density_and_tangential_momentum():
+    shape = (12, 7, 6)
+    case = cases.base_case("D3Q19", shape, psi=["rho"], g=[[0.0, 0.0], [0.0, 0.0]],
+                           bc=["pressure", "pressure", "wall", "wall", "periodic", "periodic"],
+                           bc_rho=[[1.02, 0], [0.98, 0]] + [[0, 0]] * 4)
+    s = oracle.OracleSim(case)
+    s.init_fields(0, np.full(s.shape, 1.0))
+    s.step(7)
+    f = s.populations(0)
+    e = s.e.astype(float)
+    rho = f.sum(axis=0)
+    assert np.allclose(rho[:, :, 0], 1.02, atol=1e-14)
+    assert np.allclose(rho[:, :, -1], 0.98, atol=1e-14)
+    for a in (1, 2):
+        m = np.einsum("i,izyx->zyx", e[:, a], f)
+        assert np.allclose(m[:, :, 0], 0, atol=1e-14) and np.allclose(m[:, :, -1], 0, atol=1e-14)
