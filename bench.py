@@ -1,0 +1,333 @@
+"""Throughput of the D3Q19 Shan-Chen multiphase step on GB300 (MLUPS, % HBM roofline).
+
+Workload (default): D3Q19 single-component Shan-Chen, Peng-Robinson EOS
+(a = 2/49, b = 2/21, R = 1, omega = 0.344, T = 0.6 Tc), MRT collision, 256^3
+periodic lattice, FP32, 8 droplets with seeded radii U[12, 40] at random
+non-overlapping centres. A step is one lattice time step over the whole
+lattice (density pass + collide pass). MLUPS = components * nx * ny * nz *
+steps / (seconds * 1e6).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 (torchrun) every rank advances its own lattice (independent
+replicas, weak scaling); ranks only meet at the timing barriers.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "pr256": "D3Q19 Shan-Chen PR T=0.6Tc MRT 256^3 FP32, 8 droplets (seed 1234)",
+    "exp256": "D3Q19 Shan-Chen psi=exp(-1/rho) BGK 256^3 FP32, droplet R=30",
+}
+
+
+def make_case(name):
+    from synth import cases
+    if name == "pr256":
+        case, init = cases.droplets_3d_pr(n=256)
+    elif name == "exp256":
+        case, init = cases.droplet_3d_exp(n=256)
+    else:
+        raise SystemExit("unknown workload " + name)
+    return case, init
+
+
+def algorithmic_bytes(case):
+    """Bytes each kernel must move per lattice update (DRAM, once per value):
+    collide: read K*Q populations + psi (+ U) [+ mask], write K*Q populations;
+    density: read K*Q populations [+ mask], write psi (+ U) [+ rho]."""
+    Q = 19 if case["lattice"] == "D3Q19" else 9
+    e = 8 if case.get("real") == "f64" else 4
+    K = int(case.get("ncomp", 1))
+    needs_U = any(float(a) != 0.0 for a in case.get("A", [0.0])[:K])
+    geom = any(b != "periodic" for b in case.get("bc", ["periodic"] * 6))
+    scal = K * e * (2 if needs_U else 1)
+    collide = 2 * K * Q * e + scal + (1 if geom else 0)
+    density = K * Q * e + scal + (K * e if geom else 0) + (1 if geom else 0)
+    return {"collide": collide, "density": density, "step": collide + density}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples taken while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def reduce_max(value, world, device=None):
+    """Maximum of a float over ranks (the timing rule of the benchmark)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world, device=None):
+    if world > 1:
+        import torch.distributed as dist
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def aggregate(units_per_rank, seconds_per_rank_max, world):
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    return units_per_rank * world / seconds_per_rank_max
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def oracle_sample(case, init, steps):
+    """Time `steps` oracle steps on the full lattice; returns (MLUPS, seconds, threads)."""
+    import oracle
+    s = oracle.OracleSim(case)
+    if init.get("solid") is not None:
+        s.set_geometry(init["solid"])
+    for k, r in enumerate(init["rho"]):
+        s.init_fields(k, r)
+    t0 = time.perf_counter()
+    s.step(steps)
+    dt = time.perf_counter() - t0
+    K = int(case.get("ncomp", 1))
+    nx, ny, nz = case["shape"]
+    return K * nx * ny * nz * steps / dt / 1e6, dt, oracle.threads()
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    case, init = make_case(args.workload)
+    steps = max(1, min(args.steps, args.ref_steps))
+    mlups_w, _, _ = oracle_sample(case, init, 1)                 # warm-up (page-in)
+    mlups, dt, threads = oracle_sample(case, init, steps)
+    nx, ny, nz = case["shape"]
+    sample = "%d oracle steps on the full %dx%dx%d lattice (FP64, OpenMP)" % (steps, nx, ny, nz)
+    line = {
+        "impl": "reference", "metric": "D3Q19 Shan-Chen MLUPS", "value": round(mlups, 3),
+        "unit": "MLUPS", "n_gpus": args.gpus, "steps": steps, "warmup": 1,
+        "ms_per_step": round(1e3 * dt / steps, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "shape": [nx, ny, nz], "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    from paper_2506_17713_gb300 import Lattice, lbm
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    case, init = make_case(args.workload)
+    nx, ny, nz = case["shape"]
+    K = int(case.get("ncomp", 1))
+    N = nx * ny * nz
+    lat = Lattice(case)
+    if init.get("solid") is not None:
+        lat.set_geometry(init["solid"])
+    for k, r in enumerate(init["rho"]):
+        lat.init_fields(k, r)
+    stream = lat.stream
+
+    # warm-up
+    lat.step(args.warmup)
+    torch.cuda.synchronize()
+
+    # --- timed region: K steps, device time by CUDA events on the library's stream
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world, dev)
+    torch.cuda.synchronize()
+    n0 = lat.launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    lat.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = lat.launches() - n0
+    secs = ev0.elapsed_time(ev1) / 1e3
+    barrier(world, dev)
+    clk = clocks.stop()
+    secs_max = reduce_max(secs, world, dev)
+    mlups = aggregate(K * N * args.steps, secs_max, world) / 1e6
+
+    # --- per-kernel device time (events between the kernels of every step)
+    ms, cnt = lat.profile_step(args.steps)
+    abytes = algorithmic_bytes(case)
+    t_col = ms[2] / max(cnt[2], 1) / 1e3
+    t_den = ms[0] / max(cnt[0], 1) / 1e3
+    peak, peak_kind = load_peaks()
+    ach_col = abytes["collide"] * N / t_col / 1e9
+    ach_den = abytes["density"] * N / t_den / 1e9
+    step_gbs = abytes["step"] * N * args.steps / secs / 1e9
+
+    # --- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        rho_h = torch.from_numpy(np.ascontiguousarray(init["rho"][0], dtype=np.float64)).pin_memory()
+        out_rho = torch.empty((nz, ny, nx), dtype=torch.float32).pin_memory()
+        out_u = torch.empty((3, nz, ny, nx), dtype=torch.float32).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lbm.lbm_init_fields(lat.ctx, 0, rho_h.data_ptr(), None, lbm.LBM_HOST)
+        lat.step(args.e2e_steps)
+        lbm.lbm_macroscopic(lat.ctx, 0, out_rho.data_ptr(), out_u.data_ptr(), lbm.LBM_HOST)
+        mass, mom = lat.diagnostics()
+        te = time.perf_counter() - t0
+        te_max = reduce_max(te, world, dev)
+        e2e = {"value": round(aggregate(K * N * args.e2e_steps, te_max, world) / 1e6, 1), "unit": "MLUPS",
+               "h2d_bytes_per_step": int(rho_h.numel() * 8 // args.e2e_steps),
+               "d2h_bytes_per_step": int((out_rho.numel() + out_u.numel()) * 4 // args.e2e_steps + 48),
+               "steps": args.e2e_steps,
+               "note": "init_fields from pinned host + steps + macroscopic to pinned host + diagnostics"}
+
+    if rank != 0:
+        barrier(world, dev)
+        return
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu_mlups, cpu_dt, threads = oracle_sample(case, init, args.cpu_steps)
+        cpu = {"value": round(cpu_mlups, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
+               "sample": "%d FP64 oracle steps on the full %dx%dx%d lattice (%.1f s)" % (
+                   args.cpu_steps, nx, ny, nz, cpu_dt)}
+
+    line = {
+        "metric": "D3Q19 Shan-Chen MLUPS", "value": round(mlups, 1), "unit": "MLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * secs_max / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if case.get("real") != "f64" else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "shape": [nx, ny, nz], "components": K,
+                   "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "inputs larger than L2 (two %.2f GB population buffers)" % (
+                       K * 19 * N * 4 / 1e9)},
+        "roofline": {"bound": "hbm", "kernel": "k_collide", "achieved": round(ach_col, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(ach_col / peak, 4),
+                     "peak_kind": peak_kind, "traffic": None,
+                     "bytes_per_lu": abytes["collide"], "ms_per_launch": round(t_col * 1e3, 4),
+                     "density_kernel": {"achieved": round(ach_den, 1), "frac": round(ach_den / peak, 4),
+                                        "bytes_per_lu": abytes["density"],
+                                        "ms_per_launch": round(t_den * 1e3, 4)},
+                     "step": {"bytes_per_lu": abytes["step"], "achieved": round(step_gbs, 1),
+                              "frac": round(step_gbs / peak, 4)}},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        barrier(world, dev)
+    lat.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="pr256", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--ref-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

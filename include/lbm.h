@@ -1,0 +1,191 @@
+/*
+ * lbm.h -- C ABI of the GB300 Shan-Chen multiphase lattice Boltzmann library.
+ *
+ * One time step follows arXiv 2506.17713 (JAX-LaB), Section 2:
+ *   density rho^k = sum_i f_i^k (Eq. macroeq / macroeq_mcp),
+ *   improved virtual density at solid nodes (Section 2.4, Eq. improved_virtual_density),
+ *   pseudopotential psi^k, U^k from an equation of state (Eq. eos_potential),
+ *   mixed Shan-Chen / Zhang-Chen interaction force with cross-component terms
+ *   (Eq. software_ff_force_mcmp) plus a body force,
+ *   BGK or MRT collision (Eq. collision_model) with Exact Difference Method forcing (Eq. edm),
+ *   streaming with halfway bounce-back at solids (Eq. lbe_steps),
+ *   optional constant-density x faces.
+ *
+ * Conventions (all entry points):
+ *   - Node index n = x + nx*(y + ny*z), x fastest. N = nx*ny*nz. D2Q9 has nz = 1.
+ *   - Scalar fields are [N]; vector fields are [D][N] (D = 2 for D2Q9, 3 for D3Q19);
+ *     populations are [Q][N] in the library's velocity order (lbm_velocity_set).
+ *   - Arguments tagged `where` are host pointers (LBM_HOST) or device pointers
+ *     (LBM_DEVICE) of the current CUDA device. The library copies inputs; the caller
+ *     keeps ownership of every buffer it passes.
+ *   - The library never allocates device memory: the caller allocates one device
+ *     workspace of lbm_workspace_size() bytes and keeps it alive until lbm_destroy().
+ *   - All device work is enqueued on the caller's stream (cudaStream_t passed as void*,
+ *     NULL = legacy default stream). Entry points that return data to the host
+ *     synchronise that stream.
+ *   - No exception crosses the ABI. A context is not thread safe.
+ *   - Errors are sticky: after a CUDA error or a detected instability every later
+ *     call on the context returns the same status until it is destroyed.
+ *   - Stored precision (LBM_FP32 / LBM_FP64) is also the compute precision.
+ */
+#ifndef GB300_LBM_H
+#define GB300_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID_ARG = 1, /* a pointer, size, enum or parameter is out of range */
+    LBM_ERR_WORKSPACE = 2,   /* workspace missing, misaligned (256 B) or too small */
+    LBM_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+    LBM_ERR_UNSTABLE = 4,    /* non-finite or non-positive density met in a step */
+    LBM_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    LBM_ERR_STATE = 6        /* call out of order (e.g. step before init) */
+} lbm_status;
+
+enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };
+enum { LBM_FP32 = 0, LBM_FP64 = 1 };
+enum { LBM_BGK = 0, LBM_MRT = 1 };
+/* equilibrium velocity of a component: its own bare velocity j^k / rho^k
+ * (Eq. macroeq_mcp) or the Shan-Chen common velocity sum_k j^k/tau_k / sum_k rho^k/tau_k */
+enum { LBM_UEQ_COMPONENT = 0, LBM_UEQ_COMMON = 1 };
+/* pseudopotential: from an EOS (Eq. eos_potential), psi = rho (Section 3.3.2),
+ * psi = exp(-1/rho) (Section 5) */
+enum { LBM_PSI_EOS = 0, LBM_PSI_RHO = 1, LBM_PSI_EXP = 2 };
+/* equations of state named in Section 2.2 */
+enum { LBM_EOS_CS = 0, LBM_EOS_PR = 1, LBM_EOS_VDW = 2, LBM_EOS_RK = 3, LBM_EOS_RKS = 4 };
+/* face kinds: periodic; wall (halfway bounce-back, neutral wetting); constant density
+ * (x faces only) */
+enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL = 1, LBM_BC_PRESSURE = 2 };
+enum { LBM_HOST = 0, LBM_DEVICE = 1 };
+
+/*
+ * Problem parameters (all per component k = 0, 1; entries of absent components are ignored).
+ *
+ *   tau[k]            relaxation time; kinematic viscosity c_s^2 (tau - 1/2).
+ *   mrt_s[k][m]       MRT relaxation rate of moment m of the Gram-Schmidt basis
+ *                     (D2Q9: Lallemand & Luo order rho,e,eps,jx,qx,jy,qy,pxx,pxy;
+ *                     D3Q19: d'Humieres 2002 order rho,e,eps,jx,qx,jy,qy,jz,qz,
+ *                     3pxx,3pixx,pww,piww,pxy,pyz,pxz,mx,my,mz). The stress rates are
+ *                     replaced by 1/tau[k] and the conserved ones by 0.
+ *   eos_a/b/R/omega   EOS parameters a, b, R and acentric factor omega (PR, RKS).
+ *   T_red[k]          temperature T / Tc, Tc being the exact critical temperature of
+ *                     the EOS (where dp/drho = d2p/drho2 = 0).
+ *   alpha[k]          pressure scaling alpha^k of Eq. eos_potential.
+ *   A[k]              Zhang-Chen / Shan-Chen mixing weight A_kk of Eq. software_ff_force_mcmp.
+ *   g[k][k']          interaction strengths g_kk'; g_kk = -1 for an EOS pseudopotential.
+ *   wet_phi, wet_drho virtual solid density rho_s = wet_phi * rho_ave - wet_drho
+ *                     (phi >= 1 with drho = 0 for theta <= 90 deg, phi = 1 with drho >= 0
+ *                     above), limited to [rho_min, rho_max].
+ *   body_accel[k][d]  body acceleration a^k: the body force is rho^k a^k.
+ *   bc[f]             face kinds, faces -x,+x,-y,+y,-z,+z (z faces ignored in 2-D).
+ *   bc_rho[f][k]      densities of constant-density faces.
+ *
+ * Interaction weights G_i = w_i / c_s^2 on all Q-1 links; psi = sqrt(max(0, 2 U / g_kk))
+ * with U = alpha p_EOS - c_s^2 rho for the EOS kind, and U = g_kk psi^2 / 2 otherwise.
+ * Across non-periodic faces the force and wetting stencils read the coordinate-clamped
+ * in-domain node.
+ */
+typedef struct lbm_params {
+    int lattice;     /* LBM_D2Q9 | LBM_D3Q19 */
+    int nx, ny, nz;  /* nz = 1 for D2Q9 */
+    int ncomp;       /* 1 | 2 */
+    int real;        /* LBM_FP32 | LBM_FP64 */
+    int collision;   /* LBM_BGK | LBM_MRT */
+    int velocity;    /* LBM_UEQ_COMPONENT | LBM_UEQ_COMMON */
+    double tau[2];
+    double mrt_s[2][19];
+    int psi_kind[2];
+    int eos[2];
+    double eos_a[2], eos_b[2], eos_R[2], eos_omega[2], T_red[2];
+    double alpha[2];
+    double A[2];
+    double g[2][2];
+    double wet_phi[2], wet_drho[2];
+    double rho_min[2], rho_max[2];
+    double body_accel[2][3];
+    int bc[6];
+    double bc_rho[6][2];
+} lbm_params;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Bytes of device workspace needed for these parameters (Section 2.6 data layout:
+ * one population array per component, here two of them for pull streaming).
+ * Returns LBM_ERR_INVALID_ARG for invalid parameters. */
+lbm_status lbm_workspace_size(const lbm_params* p, size_t* bytes);
+
+/* Create a context on the current CUDA device. d_workspace: device pointer, 256-byte
+ * aligned, at least lbm_workspace_size() bytes, owned by the caller; stream: the
+ * caller's cudaStream_t. On success *out receives the context (host memory owned by
+ * the library, freed by lbm_destroy). The geometry starts all-fluid. */
+lbm_status lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void* stream,
+                      lbm_ctx** out);
+
+/* Solid mask, N bytes, 1 = solid, 0 = fluid (Sections 3.4, 2.4). Builds the list of
+ * boundary solids (solids read by a fluid node's stencil). Invalidates the fields:
+ * call lbm_init_fields or lbm_set_populations afterwards. */
+lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* solid, int where);
+
+/* Populations of component comp := f^eq(rho, u) at fluid nodes (Eq. macroeq with the
+ * second-order equilibrium). rho: [N] doubles; u: [D][N] doubles or NULL for rest. */
+lbm_status lbm_init_fields(lbm_ctx* ctx, int comp, const double* rho, const double* u,
+                           int where);
+
+/* Advance nsteps time steps (Eq. lbe_steps), enqueued on the context stream. */
+lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
+
+/* Density and velocity u = (sum_i f_i e_i + F/2) / rho of component comp, or of the
+ * mixture (sum over components) for comp = -1, at the current time (Eq. after Eq. edm).
+ * Element type = the context's real type (float for LBM_FP32, double for LBM_FP64).
+ * rho: [N], u: [D][N]; either may be NULL; solids give 0. */
+lbm_status lbm_macroscopic(lbm_ctx* ctx, int comp, void* rho, void* u, int where);
+
+/* Total mass sum_x rho^k and momentum sum_x (j^k + F^k/2) per component, summed in
+ * FP64 in a fixed order (deterministic). mass: [ncomp]; momentum: [ncomp][3].
+ * residual (may be NULL): ||u - u_prev||_2 / ||u||_2 of the mixture velocity over fluid
+ * nodes, u_prev being the velocity at the previous call that asked for a residual
+ * (1.0 on the first such call). Synchronises; reports LBM_ERR_UNSTABLE if a step met a
+ * non-finite or non-positive density. */
+lbm_status lbm_diagnostics(lbm_ctx* ctx, double* mass, double* momentum, double* residual);
+
+/* Post-stream populations of component comp, [Q][N] of the real type (checkpoint /
+ * inspection). lbm_set_populations restores them exactly (bit for bit), except for the
+ * populations that constant-density faces recompute. */
+lbm_status lbm_get_populations(lbm_ctx* ctx, int comp, void* f, int where);
+lbm_status lbm_set_populations(lbm_ctx* ctx, int comp, const void* f, int where);
+
+/* Velocity set in the library's order: e: [Q][3] ints, w: [Q] doubles (either NULL). */
+lbm_status lbm_velocity_set(const lbm_ctx* ctx, int* q, int* e, double* w);
+
+/* Wait for the context stream; returns the sticky status. */
+lbm_status lbm_sync(lbm_ctx* ctx);
+
+/* Advance nsteps time steps like lbm_step, recording CUDA events on the context
+ * stream between the kernels of every step, then synchronise. ms[0], ms[1], ms[2]
+ * receive the summed device time (milliseconds) of the density, virtual-density and
+ * collide kernels; launches[0..2] the number of launches of each. Timing aid for the
+ * benchmark; the arithmetic is that of lbm_step. */
+lbm_status lbm_profile_step(lbm_ctx* ctx, int nsteps, double* ms, long long* launches);
+
+/* Number of kernels this context has launched since creation. */
+long long lbm_kernel_launches(const lbm_ctx* ctx);
+
+/* Absolute temperature T_red * Tc used for component comp (EOS pseudopotential). */
+lbm_status lbm_temperature(const lbm_ctx* ctx, int comp, double* T);
+
+/* Release the context (not the caller's workspace). NULL is ignored. */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Static string naming a status. */
+const char* lbm_status_str(lbm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_LBM_H */

@@ -1,0 +1,85 @@
+// Kernel argument block shared by the C-ABI layer and the kernel translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+enum : int { PSI_EOS = 0, PSI_RHO = 1, PSI_EXP = 2 };
+enum : int { EOS_CS = 0, EOS_PR = 1, EOS_VDW = 2, EOS_RK = 3, EOS_RKS = 4 };
+enum : int { BC_PERIODIC = 0, BC_WALL = 1, BC_PRESSURE = 2 };
+enum : int { COLL_BGK = 0, COLL_MRT = 1 };
+
+// status word slots (device int[8])
+enum : int { ST_UNSTABLE = 0, ST_PSI_CLAMP = 1, ST_TIMEOUT = 2 };
+
+// Physical parameters in the compute type T, resolved on the host.
+template <typename T>
+struct Params {
+    int nx, ny, nz;
+    long long N;
+    int ncomp;
+    int collision;
+    int common_velocity;
+    int needs_U;         // some component mixes in the Zhang-Chen force (A != 0)
+    int bc[6];
+    int psi_kind[2];
+    int eos[2];
+    T omega[2];          // 1 / tau
+    T rates[2][19];      // MRT rates, stress = 1/tau, conserved = 0
+    T eos_a[2], eos_b[2], RT[2], alphaT[2], sqrtT[2];
+    T alpha[2], A[2], g[2][2];
+    T wet_phi[2], wet_drho[2], rho_min[2], rho_max[2];
+    T accel[2][3];
+    T bc_rho[2][2];      // [x side][component]
+};
+
+// Operations dispatched to the per-(lattice, type) translation units.
+enum : int {
+    OP_DENSITY = 0,      // rho, psi (U) at fluid nodes from the pre-stream buffer
+    OP_VIRTUAL = 1,      // virtual density / psi at boundary solids
+    OP_COLLIDE = 2,      // fused gather + force + collision + EDM -> post-collision buffer
+    OP_INIT_EQ = 3,      // post-stream populations := f^eq(rho0, u0)
+    OP_SET_POPS = 4,     // post-stream populations := given array
+    OP_GET_POPS = 5,     // gather post-stream populations into an array
+    OP_MACRO = 6,        // rho, u = (j + F/2) / rho into arrays
+    OP_DIAG = 7          // mass / momentum / residual partial sums (deterministic)
+};
+
+template <typename T>
+struct KArgs {
+    Params<T> p;
+    const T* f_src;      // pre-stream (post-collision) populations, [K][Q][N]
+    T* f_dst;            // next pre-stream buffer
+    T* psi;              // [K][N]
+    T* U;                // [K][N]
+    T* rho;              // [K][N] (read by the virtual-density pass)
+    const uint8_t* solid;
+    const int* bsolid;   // boundary-solid node list
+    int n_bsolid;
+    int geom;            // solids present or a non-periodic face
+    int* status;         // device status word
+    // operation-specific
+    int comp;            // component (-1 = mixture for OP_MACRO)
+    const double* in_rho;
+    const double* in_u;
+    const T* in_f;
+    T* out_rho;
+    T* out_u;
+    T* out_f;
+    T* u_prev;           // [D][N] mixture velocity at the last residual request
+    int want_residual;
+    double* partials;    // [diag_blocks][8]
+    double* totals;      // [8]
+    cudaStream_t stream;
+};
+
+constexpr int DIAG_BLOCKS = 1024;
+constexpr int DIAG_THREADS = 256;
+
+template <class L, typename T>
+cudaError_t run(int op, const KArgs<T>& a);
+
+}  // namespace lbm

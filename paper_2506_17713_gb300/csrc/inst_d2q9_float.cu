@@ -1,0 +1,7 @@
+// Kernel instantiations for the D2Q9 lattice in float (one translation unit per
+// lattice and type so that the build compiles them in parallel).
+#include "kernels.cuh"
+
+namespace lbm {
+template cudaError_t run<D2Q9, float>(int op, const KArgs<float>& a);
+}  // namespace lbm

@@ -1,0 +1,777 @@
+// C-ABI entry points (include/lbm.h): parameter validation, workspace carving,
+// geometry set-up, and the launch sequence of one time step.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "args.h"
+#include "lattice.cuh"
+#include "lbm.h"
+
+using namespace lbm;
+
+struct lbm_ctx {
+    lbm_params prm;
+    int Q, D;
+    long long N;
+    size_t elt;             // bytes per stored value
+    char* ws;
+    size_t ws_bytes;
+    void* fbuf[2];          // population buffers, [K][Q][N]
+    int cur;                // buffer holding the pre-stream populations
+    void* psi;
+    void* U;
+    void* rho;
+    uint8_t* solid;
+    int* bsolid;
+    int n_bsolid;
+    void* u_prev;
+    int* status;
+    double* partials;
+    double* totals;
+    int geom;               // solids present or a non-periodic face
+    int any_solid;
+    bool faces_open;        // some face is not periodic
+    bool init[2];
+    bool have_uprev;
+    cudaStream_t stream;
+    lbm_status sticky;
+    long long launches;
+    double T[2];
+    Params<float> pf;
+    Params<double> pd;
+};
+
+// ---------------------------------------------------------------------------
+// Critical temperature of an EOS: the isotherm through the critical point has
+// dp/drho = d2p/drho2 = 0. Writing p = R T u(rho) - a c(T) s(rho), the two
+// conditions give u' s'' - u'' s' = 0 for rho_c and R T_c c(T_c) = a s'/u'. The
+// derivatives come from second-order forward-mode (hyper-dual) arithmetic.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct HD {
+    double v, d, dd;  // value, first and second derivative
+};
+HD operator+(HD a, HD b) { return {a.v + b.v, a.d + b.d, a.dd + b.dd}; }
+HD operator-(HD a, HD b) { return {a.v - b.v, a.d - b.d, a.dd - b.dd}; }
+HD operator*(HD a, HD b) { return {a.v * b.v, a.d * b.v + a.v * b.d, a.dd * b.v + 2 * a.d * b.d + a.v * b.dd}; }
+HD operator/(HD a, HD b)
+{
+    const double q = a.v / b.v;
+    const double qd = (a.d - q * b.d) / b.v;
+    const double qdd = (a.dd - 2 * qd * b.d - q * b.dd) / b.v;
+    return {q, qd, qdd};
+}
+HD cst(double c) { return {c, 0, 0}; }
+
+// repulsive part u (p_rep = R T u) and attractive part s (p_att = a c(T) s)
+void eos_parts(int eos, double b, double rho, HD& u, HD& s)
+{
+    const HD r = {rho, 1, 0};
+    const HD one = cst(1);
+    switch (eos) {
+    case EOS_CS: {
+        const HD e = cst(b / 4) * r;
+        u = r * (one + e + e * e - e * e * e) / ((one - e) * (one - e) * (one - e));
+        s = r * r;
+        break;
+    }
+    case EOS_PR:
+        u = r / (one - cst(b) * r);
+        s = r * r / (one + cst(2 * b) * r - cst(b * b) * r * r);
+        break;
+    case EOS_VDW:
+        u = r / (one - cst(b) * r);
+        s = r * r;
+        break;
+    default:  // RK, RKS
+        u = r / (one - cst(b) * r);
+        s = r * r / (one + cst(b) * r);
+        break;
+    }
+}
+
+double critical_temperature(int eos, double a, double b, double R)
+{
+    const double pole = eos == EOS_CS ? 4.0 / b : 1.0 / b;
+    auto h = [&](double rho) {
+        HD u, s;
+        eos_parts(eos, b, rho, u, s);
+        return u.d * s.dd - u.dd * s.d;
+    };
+    // h > 0 at low density, < 0 near the pole: bracket by a scan, then bisect
+    double lo = 1e-6 * pole, hi = lo;
+    const int n = 4000;
+    for (int m = 1; m < n; ++m) {
+        const double r = pole * m / n;
+        if (h(r) <= 0) { hi = r; break; }
+        lo = r;
+    }
+    if (hi <= lo) return NAN;
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (h(mid) > 0) lo = mid; else hi = mid;
+    }
+    HD u, s;
+    eos_parts(eos, b, 0.5 * (lo + hi), u, s);
+    const double x = a * s.d / (R * u.d);  // = T_c c(T_c)
+    return eos == EOS_RK ? std::pow(x, 2.0 / 3.0) : x;  // RK: c(T) = T^-1/2
+}
+
+double eos_alpha(int eos, double omega, double Tr)
+{
+    if (eos != EOS_PR && eos != EOS_RKS) return 1.0;
+    const double m = eos == EOS_PR ? 0.37464 + 1.54226 * omega - 0.26992 * omega * omega
+                                   : 0.480 + 1.574 * omega - 0.176 * omega * omega;
+    const double s = 1.0 + m * (1.0 - std::sqrt(Tr));
+    return s * s;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct Layout {
+    size_t f, psi, U, rho, solid, bsolid, uprev, status, partials, totals, total;
+};
+
+bool fin(double v) { return std::isfinite(v); }
+
+lbm_status validate(const lbm_params* p)
+{
+    if (!p) return LBM_ERR_INVALID_ARG;
+    if (p->lattice != LBM_D2Q9 && p->lattice != LBM_D3Q19) return LBM_ERR_INVALID_ARG;
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->ny > 65535 || p->nz > 65535) return LBM_ERR_INVALID_ARG;
+    if (p->lattice == LBM_D2Q9 && p->nz != 1) return LBM_ERR_INVALID_ARG;
+    if (p->ncomp != 1 && p->ncomp != 2) return LBM_ERR_INVALID_ARG;
+    if (p->real != LBM_FP32 && p->real != LBM_FP64) return LBM_ERR_INVALID_ARG;
+    if (p->collision != LBM_BGK && p->collision != LBM_MRT) return LBM_ERR_INVALID_ARG;
+    if (p->velocity != LBM_UEQ_COMPONENT && p->velocity != LBM_UEQ_COMMON) return LBM_ERR_INVALID_ARG;
+    const int nf = p->lattice == LBM_D2Q9 ? 4 : 6;
+    for (int f = 0; f < 6; ++f) {
+        const int b = p->bc[f];
+        if (f >= nf) continue;
+        if (b != LBM_BC_PERIODIC && b != LBM_BC_WALL && b != LBM_BC_PRESSURE) return LBM_ERR_INVALID_ARG;
+        if (b == LBM_BC_PRESSURE && f >= 2) return LBM_ERR_INVALID_ARG;  // x faces only
+    }
+    for (int a = 0; a < nf / 2; ++a)  // periodicity is a property of the axis
+        if ((p->bc[2 * a] == LBM_BC_PERIODIC) != (p->bc[2 * a + 1] == LBM_BC_PERIODIC)) return LBM_ERR_INVALID_ARG;
+    if ((p->bc[0] == LBM_BC_PRESSURE || p->bc[1] == LBM_BC_PRESSURE) && p->nx < 3) return LBM_ERR_INVALID_ARG;
+    for (int k = 0; k < p->ncomp; ++k) {
+        if (!(p->tau[k] > 0.5) || !fin(p->tau[k])) return LBM_ERR_INVALID_ARG;
+        if (p->collision == LBM_MRT)
+            for (int m = 0; m < 19; ++m)
+                if (!fin(p->mrt_s[k][m]) || p->mrt_s[k][m] < 0 || p->mrt_s[k][m] >= 2) return LBM_ERR_INVALID_ARG;
+        const int pk = p->psi_kind[k];
+        if (pk != LBM_PSI_EOS && pk != LBM_PSI_RHO && pk != LBM_PSI_EXP) return LBM_ERR_INVALID_ARG;
+        if (pk == LBM_PSI_EOS) {
+            if (p->eos[k] < LBM_EOS_CS || p->eos[k] > LBM_EOS_RKS) return LBM_ERR_INVALID_ARG;
+            if (!(p->eos_a[k] > 0) || !(p->eos_b[k] > 0) || !(p->eos_R[k] > 0) || !(p->T_red[k] > 0))
+                return LBM_ERR_INVALID_ARG;
+            if (!fin(p->eos_omega[k]) || !fin(p->alpha[k])) return LBM_ERR_INVALID_ARG;
+            if (p->g[k][k] == 0.0) return LBM_ERR_INVALID_ARG;
+        }
+        for (int kp = 0; kp < p->ncomp; ++kp)
+            if (!fin(p->g[k][kp])) return LBM_ERR_INVALID_ARG;
+        if (!fin(p->A[k]) || !fin(p->wet_phi[k]) || !fin(p->wet_drho[k])) return LBM_ERR_INVALID_ARG;
+        if (std::isnan(p->rho_min[k]) || std::isnan(p->rho_max[k]) || p->rho_min[k] > p->rho_max[k])
+            return LBM_ERR_INVALID_ARG;
+        for (int d = 0; d < 3; ++d)
+            if (!fin(p->body_accel[k][d])) return LBM_ERR_INVALID_ARG;
+        for (int f = 0; f < 2; ++f)
+            if (p->bc[f] == LBM_BC_PRESSURE && !(p->bc_rho[f][k] > 0)) return LBM_ERR_INVALID_ARG;
+    }
+    if (p->ncomp == 2 && p->g[0][1] != p->g[1][0]) return LBM_ERR_INVALID_ARG;
+    return LBM_OK;
+}
+
+bool needs_U(const lbm_params* p)
+{
+    for (int k = 0; k < p->ncomp; ++k)
+        if (p->A[k] != 0.0) return true;
+    return false;
+}
+
+Layout layout_of(const lbm_params* p)
+{
+    const int Q = p->lattice == LBM_D2Q9 ? 9 : 19;
+    const int D = p->lattice == LBM_D2Q9 ? 2 : 3;
+    const size_t N = (size_t)p->nx * p->ny * p->nz;
+    const size_t e = p->real == LBM_FP64 ? 8 : 4;
+    const size_t K = (size_t)p->ncomp;
+    Layout L;
+    size_t off = 0;
+    L.f = off;        off += 2 * align256(K * Q * N * e);
+    L.psi = off;      off += align256(K * N * e);
+    L.U = off;        off += needs_U(p) ? align256(K * N * e) : 0;
+    L.rho = off;      off += align256(K * N * e);
+    L.solid = off;    off += align256(N);
+    L.bsolid = off;   off += align256(N * sizeof(int));
+    L.uprev = off;    off += align256((size_t)D * N * e);
+    L.status = off;   off += 256;
+    L.partials = off; off += align256(sizeof(double) * 8 * DIAG_BLOCKS);
+    L.totals = off;   off += 256;
+    L.total = off;
+    return L;
+}
+
+template <typename T>
+void fill_params(const lbm_ctx* c, Params<T>& P)
+{
+    const lbm_params* p = &c->prm;
+    std::memset(&P, 0, sizeof(P));
+    P.nx = p->nx; P.ny = p->ny; P.nz = p->nz;
+    P.N = c->N;
+    P.ncomp = p->ncomp;
+    P.collision = p->collision == LBM_MRT ? COLL_MRT : COLL_BGK;
+    P.common_velocity = p->velocity == LBM_UEQ_COMMON;
+    P.needs_U = needs_U(p);
+    for (int f = 0; f < 6; ++f) P.bc[f] = (c->D == 2 && f >= 4) ? BC_PERIODIC : p->bc[f];
+    const bool d2 = p->lattice == LBM_D2Q9;
+    for (int k = 0; k < 2; ++k) {
+        const int kk = k < p->ncomp ? k : 0;
+        P.psi_kind[k] = p->psi_kind[kk];
+        P.eos[k] = p->eos[kk];
+        P.omega[k] = (T)(1.0 / p->tau[kk]);
+        for (int m = 0; m < 19; ++m) {
+            const bool cons = d2 ? D2Q9::conserved(m) : D3Q19::conserved(m);
+            const bool str = d2 ? D2Q9::stress(m) : D3Q19::stress(m);
+            P.rates[k][m] = cons ? T(0) : (str ? (T)(1.0 / p->tau[kk]) : (T)p->mrt_s[kk][m]);
+        }
+        P.eos_a[k] = (T)p->eos_a[kk];
+        P.eos_b[k] = (T)p->eos_b[kk];
+        P.RT[k] = (T)(p->eos_R[kk] * c->T[kk]);
+        P.alphaT[k] = (T)eos_alpha(p->eos[kk], p->eos_omega[kk], p->T_red[kk]);
+        P.sqrtT[k] = (T)std::sqrt(c->T[kk]);
+        P.alpha[k] = (T)p->alpha[kk];
+        P.A[k] = (T)p->A[kk];
+        for (int kp = 0; kp < 2; ++kp) P.g[k][kp] = (T)p->g[kk][kp < p->ncomp ? kp : 0];
+        P.wet_phi[k] = (T)p->wet_phi[kk];
+        P.wet_drho[k] = (T)p->wet_drho[kk];
+        P.rho_min[k] = (T)p->rho_min[kk];
+        P.rho_max[k] = (T)p->rho_max[kk];
+        for (int d = 0; d < 3; ++d) P.accel[k][d] = (T)((d2 && d == 2) ? 0.0 : p->body_accel[kk][d]);
+        for (int s = 0; s < 2; ++s) P.bc_rho[s][k] = (T)p->bc_rho[s][kk];
+    }
+}
+
+template <typename T>
+KArgs<T> base_args(lbm_ctx* c, const Params<T>& P)
+{
+    KArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.p = P;
+    a.f_src = (const T*)c->fbuf[c->cur];
+    a.f_dst = (T*)c->fbuf[c->cur ^ 1];
+    a.psi = (T*)c->psi;
+    a.U = (T*)c->U;
+    a.rho = (T*)c->rho;
+    a.solid = c->solid;
+    a.bsolid = c->bsolid;
+    a.n_bsolid = c->n_bsolid;
+    a.geom = c->geom;
+    a.status = c->status;
+    a.u_prev = (T*)c->u_prev;
+    a.partials = c->partials;
+    a.totals = c->totals;
+    a.stream = c->stream;
+    a.comp = 0;
+    return a;
+}
+
+template <typename T>
+cudaError_t dispatch(lbm_ctx* c, int op, const KArgs<T>& a)
+{
+    cudaError_t e = c->prm.lattice == LBM_D2Q9 ? run<D2Q9, T>(op, a) : run<D3Q19, T>(op, a);
+    if (e == cudaSuccess) {
+        if (op == OP_DIAG) c->launches += 2;
+        else if (op != OP_VIRTUAL || c->n_bsolid > 0) c->launches += 1;
+    }
+    return e;
+}
+
+lbm_status fail_cuda(lbm_ctx* c, cudaError_t e)
+{
+    if (e != cudaSuccess) {
+        c->sticky = LBM_ERR_CUDA;
+        return LBM_ERR_CUDA;
+    }
+    return LBM_OK;
+}
+
+// rho, psi, U at fluid nodes and boundary solids for the current time level
+template <typename T>
+cudaError_t fields_pass(lbm_ctx* c, const Params<T>& P)
+{
+    KArgs<T> a = base_args<T>(c, P);
+    cudaError_t e = dispatch<T>(c, OP_DENSITY, a);
+    if (e == cudaSuccess && c->n_bsolid > 0) e = dispatch<T>(c, OP_VIRTUAL, a);
+    return e;
+}
+
+template <typename T>
+cudaError_t step_once(lbm_ctx* c, const Params<T>& P)
+{
+    cudaError_t e = fields_pass<T>(c, P);
+    if (e != cudaSuccess) return e;
+    KArgs<T> a = base_args<T>(c, P);
+    e = dispatch<T>(c, OP_COLLIDE, a);
+    if (e == cudaSuccess) c->cur ^= 1;
+    return e;
+}
+
+lbm_status check_status_word(lbm_ctx* c)
+{
+    int st[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(st, c->status, sizeof(st), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail_cuda(c, e);
+    if (st[ST_TIMEOUT]) c->sticky = LBM_ERR_TIMEOUT;
+    else if (st[ST_UNSTABLE]) c->sticky = LBM_ERR_UNSTABLE;
+    return c->sticky;
+}
+
+bool ready(const lbm_ctx* c) { return c->init[0] && (c->prm.ncomp < 2 || c->init[1]); }
+
+// host-side neighbour rule of the stencils (periodic wrap, clamp elsewhere)
+long long host_nb(const lbm_ctx* c, int x, int y, int z, int ex, int ey, int ez)
+{
+    const lbm_params* p = &c->prm;
+    int v[3] = {x + ex, y + ey, z + ez};
+    const int n[3] = {p->nx, p->ny, p->nz};
+    for (int a = 0; a < 3; ++a) {
+        const bool per = (c->D == 2 && a == 2) || p->bc[2 * a] == LBM_BC_PERIODIC;
+        if (v[a] < 0) v[a] = per ? v[a] + n[a] : 0;
+        else if (v[a] >= n[a]) v[a] = per ? v[a] - n[a] : n[a] - 1;
+    }
+    return (long long)v[0] + (long long)p->nx * ((long long)v[1] + (long long)p->ny * v[2]);
+}
+
+template <class L>
+int build_boundary_list(const lbm_ctx* c, const uint8_t* solid, std::vector<int>& out)
+{
+    const lbm_params* p = &c->prm;
+    out.clear();
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                const long long n = (long long)x + (long long)p->nx * ((long long)y + (long long)p->ny * z);
+                if (!solid[n]) continue;
+                for (int i = 1; i < L::Q; ++i)
+                    if (!solid[host_nb(c, x, y, z, L::ex(i), L::ey(i), L::ez(i))]) {
+                        out.push_back((int)n);
+                        break;
+                    }
+            }
+    return (int)out.size();
+}
+
+// The second population buffer doubles as staging space for host transfers.
+void* staging(lbm_ctx* c) { return c->fbuf[c->cur ^ 1]; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Entry points
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+lbm_status lbm_workspace_size(const lbm_params* p, size_t* bytes)
+{
+    if (!bytes) return LBM_ERR_INVALID_ARG;
+    const lbm_status s = validate(p);
+    if (s != LBM_OK) return s;
+    *bytes = layout_of(p).total;
+    return LBM_OK;
+}
+
+lbm_status lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void* stream, lbm_ctx** out)
+{
+    if (!out) return LBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    lbm_status s = validate(p);
+    if (s != LBM_OK) return s;
+    const Layout L = layout_of(p);
+    if (!d_workspace || bytes < L.total || ((uintptr_t)d_workspace & 255)) return LBM_ERR_WORKSPACE;
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return LBM_ERR_INVALID_ARG;
+    c->prm = *p;
+    c->Q = p->lattice == LBM_D2Q9 ? 9 : 19;
+    c->D = p->lattice == LBM_D2Q9 ? 2 : 3;
+    c->N = (long long)p->nx * p->ny * p->nz;
+    c->elt = p->real == LBM_FP64 ? 8 : 4;
+    c->ws = (char*)d_workspace;
+    c->ws_bytes = bytes;
+    const size_t fbytes = align256((size_t)p->ncomp * c->Q * c->N * c->elt);
+    c->fbuf[0] = c->ws + L.f;
+    c->fbuf[1] = c->ws + L.f + fbytes;
+    c->cur = 0;
+    c->psi = c->ws + L.psi;
+    c->U = needs_U(p) ? (void*)(c->ws + L.U) : nullptr;
+    c->rho = c->ws + L.rho;
+    c->solid = (uint8_t*)(c->ws + L.solid);
+    c->bsolid = (int*)(c->ws + L.bsolid);
+    c->u_prev = c->ws + L.uprev;
+    c->status = (int*)(c->ws + L.status);
+    c->partials = (double*)(c->ws + L.partials);
+    c->totals = (double*)(c->ws + L.totals);
+    c->stream = (cudaStream_t)stream;
+    c->sticky = LBM_OK;
+    c->faces_open = false;
+    for (int f = 0; f < (c->D == 2 ? 4 : 6); ++f) c->faces_open |= p->bc[f] != LBM_BC_PERIODIC;
+    c->geom = c->faces_open;
+    for (int k = 0; k < 2; ++k) {
+        c->T[k] = 0.0;
+        if (k < p->ncomp && p->psi_kind[k] == LBM_PSI_EOS) {
+            const double tc = critical_temperature(p->eos[k], p->eos_a[k], p->eos_b[k], p->eos_R[k]);
+            if (!std::isfinite(tc)) { delete c; return LBM_ERR_INVALID_ARG; }
+            c->T[k] = p->T_red[k] * tc;
+        }
+    }
+    fill_params<float>(c, c->pf);
+    fill_params<double>(c, c->pd);
+    cudaError_t e = cudaMemsetAsync(c->solid, 0, (size_t)c->N, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, 256, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) { delete c; return LBM_ERR_CUDA; }
+    *out = c;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* solid, int where)
+{
+    if (!c || !solid || (where != LBM_HOST && where != LBM_DEVICE)) return LBM_ERR_INVALID_ARG;
+    if (c->sticky != LBM_OK) return c->sticky;
+    std::vector<uint8_t> h((size_t)c->N);
+    cudaError_t e;
+    if (where == LBM_DEVICE) {
+        e = cudaMemcpyAsync(h.data(), solid, (size_t)c->N, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return fail_cuda(c, e);
+    } else {
+        std::memcpy(h.data(), solid, (size_t)c->N);
+    }
+    c->any_solid = 0;
+    for (auto& v : h) {
+        v = v ? 1 : 0;
+        c->any_solid |= v;
+    }
+    std::vector<int> list;
+    c->n_bsolid = c->D == 2 ? build_boundary_list<D2Q9>(c, h.data(), list)
+                            : build_boundary_list<D3Q19>(c, h.data(), list);
+    e = cudaMemcpyAsync(c->solid, h.data(), (size_t)c->N, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && c->n_bsolid > 0)
+        e = cudaMemcpyAsync(c->bsolid, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail_cuda(c, e);
+    c->geom = c->faces_open || c->any_solid;
+    c->init[0] = c->init[1] = false;
+    c->have_uprev = false;
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+template <typename T>
+lbm_status init_fields_t(lbm_ctx* c, int comp, const double* rho, const double* u, int where, const Params<T>& P)
+{
+    const double* drho = rho;
+    const double* du = u;
+    cudaError_t e = cudaSuccess;
+    if (where == LBM_HOST) {
+        // stage through the idle population buffer (it is at least (1 + D) N doubles)
+        double* st = (double*)staging(c);
+        e = cudaMemcpyAsync(st, rho, sizeof(double) * c->N, cudaMemcpyHostToDevice, c->stream);
+        drho = st;
+        if (e == cudaSuccess && u) {
+            e = cudaMemcpyAsync(st + c->N, u, sizeof(double) * c->D * c->N, cudaMemcpyHostToDevice, c->stream);
+            du = st + c->N;
+        }
+        if (e != cudaSuccess) return fail_cuda(c, e);
+    }
+    KArgs<T> a = base_args<T>(c, P);
+    a.f_dst = (T*)c->fbuf[c->cur];
+    a.comp = comp;
+    a.in_rho = drho;
+    a.in_u = du;
+    e = dispatch<T>(c, OP_INIT_EQ, a);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail_cuda(c, e);
+    c->init[comp] = true;
+    c->have_uprev = false;
+    return LBM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_init_fields(lbm_ctx* c, int comp, const double* rho, const double* u, int where)
+{
+    if (!c || !rho || comp < 0 || comp >= c->prm.ncomp || (where != LBM_HOST && where != LBM_DEVICE))
+        return LBM_ERR_INVALID_ARG;
+    if (c->sticky != LBM_OK) return c->sticky;
+    return c->elt == 8 ? init_fields_t<double>(c, comp, rho, u, where, c->pd)
+                       : init_fields_t<float>(c, comp, rho, u, where, c->pf);
+}
+
+lbm_status lbm_step(lbm_ctx* c, int nsteps)
+{
+    if (!c || nsteps < 0) return LBM_ERR_INVALID_ARG;
+    if (c->sticky != LBM_OK) return c->sticky;
+    if (!ready(c)) return LBM_ERR_STATE;
+    for (int s = 0; s < nsteps; ++s) {
+        const cudaError_t e = c->elt == 8 ? step_once<double>(c, c->pd) : step_once<float>(c, c->pf);
+        if (e != cudaSuccess) return fail_cuda(c, e);
+    }
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+template <typename T>
+lbm_status macro_t(lbm_ctx* c, int comp, void* rho, void* u, int where, const Params<T>& P)
+{
+    cudaError_t e = fields_pass<T>(c, P);
+    if (e != cudaSuccess) return fail_cuda(c, e);
+    KArgs<T> a = base_args<T>(c, P);
+    a.comp = comp;
+    T* st = (T*)staging(c);
+    a.out_rho = rho ? (where == LBM_HOST ? st : (T*)rho) : nullptr;
+    a.out_u = u ? (where == LBM_HOST ? st + c->N : (T*)u) : nullptr;
+    e = dispatch<T>(c, OP_MACRO, a);
+    if (e == cudaSuccess && where == LBM_HOST) {
+        if (rho) e = cudaMemcpyAsync(rho, st, sizeof(T) * c->N, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess && u)
+            e = cudaMemcpyAsync(u, st + c->N, sizeof(T) * c->D * c->N, cudaMemcpyDeviceToHost, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail_cuda(c, e);
+    return check_status_word(c);
+}
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_macroscopic(lbm_ctx* c, int comp, void* rho, void* u, int where)
+{
+    if (!c || comp < -1 || comp >= c->prm.ncomp || (where != LBM_HOST && where != LBM_DEVICE))
+        return LBM_ERR_INVALID_ARG;
+    if (c->sticky != LBM_OK) return c->sticky;
+    if (!ready(c)) return LBM_ERR_STATE;
+    return c->elt == 8 ? macro_t<double>(c, comp, rho, u, where, c->pd)
+                       : macro_t<float>(c, comp, rho, u, where, c->pf);
+}
+
+}  // extern "C"
+
+namespace {
+template <typename T>
+lbm_status diag_t(lbm_ctx* c, double* mass, double* mom, double* residual, const Params<T>& P)
+{
+    cudaError_t e = fields_pass<T>(c, P);
+    if (e != cudaSuccess) return fail_cuda(c, e);
+    double tot[8];
+    KArgs<T> a = base_args<T>(c, P);
+    a.want_residual = 0;
+    e = dispatch<T>(c, OP_DIAG, a);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tot, c->totals, sizeof(tot), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail_cuda(c, e);
+    for (int k = 0; k < c->prm.ncomp; ++k) {
+        if (mass) mass[k] = tot[k];
+        if (mom)
+            for (int d = 0; d < 3; ++d) mom[3 * k + d] = tot[2 + 3 * k + d];
+    }
+    if (residual) {
+        a.want_residual = 1;
+        e = dispatch<T>(c, OP_DIAG, a);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tot, c->totals, sizeof(tot), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return fail_cuda(c, e);
+        *residual = (c->have_uprev && tot[1] > 0) ? std::sqrt(tot[0] / tot[1]) : 1.0;
+        c->have_uprev = true;
+    }
+    return check_status_word(c);
+}
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_diagnostics(lbm_ctx* c, double* mass, double* momentum, double* residual)
+{
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (c->sticky != LBM_OK) return c->sticky;
+    if (!ready(c)) return LBM_ERR_STATE;
+    return c->elt == 8 ? diag_t<double>(c, mass, momentum, residual, c->pd)
+                       : diag_t<float>(c, mass, momentum, residual, c->pf);
+}
+
+}  // extern "C"
+
+namespace {
+template <typename T>
+lbm_status get_pops_t(lbm_ctx* c, int comp, void* f, int where, const Params<T>& P)
+{
+    KArgs<T> a = base_args<T>(c, P);
+    a.comp = comp;
+    T* st = (T*)staging(c);
+    a.out_f = where == LBM_HOST ? st : (T*)f;
+    cudaError_t e = dispatch<T>(c, OP_GET_POPS, a);
+    if (e == cudaSuccess && where == LBM_HOST)
+        e = cudaMemcpyAsync(f, st, sizeof(T) * c->Q * c->N, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return fail_cuda(c, e);
+}
+template <typename T>
+lbm_status set_pops_t(lbm_ctx* c, int comp, const void* f, int where, const Params<T>& P)
+{
+    KArgs<T> a = base_args<T>(c, P);
+    a.comp = comp;
+    a.f_dst = (T*)c->fbuf[c->cur];
+    const T* src = (const T*)f;
+    cudaError_t e = cudaSuccess;
+    if (where == LBM_HOST) {
+        T* st = (T*)staging(c);
+        e = cudaMemcpyAsync(st, f, sizeof(T) * c->Q * c->N, cudaMemcpyHostToDevice, c->stream);
+        src = st;
+    }
+    a.in_f = src;
+    if (e == cudaSuccess) e = dispatch<T>(c, OP_SET_POPS, a);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail_cuda(c, e);
+    c->init[comp] = true;
+    c->have_uprev = false;
+    return LBM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_get_populations(lbm_ctx* c, int comp, void* f, int where)
+{
+    if (!c || !f || comp < 0 || comp >= c->prm.ncomp || (where != LBM_HOST && where != LBM_DEVICE))
+        return LBM_ERR_INVALID_ARG;
+    if (c->sticky != LBM_OK) return c->sticky;
+    if (!c->init[comp]) return LBM_ERR_STATE;
+    return c->elt == 8 ? get_pops_t<double>(c, comp, f, where, c->pd) : get_pops_t<float>(c, comp, f, where, c->pf);
+}
+
+lbm_status lbm_set_populations(lbm_ctx* c, int comp, const void* f, int where)
+{
+    if (!c || !f || comp < 0 || comp >= c->prm.ncomp || (where != LBM_HOST && where != LBM_DEVICE))
+        return LBM_ERR_INVALID_ARG;
+    if (c->sticky != LBM_OK) return c->sticky;
+    return c->elt == 8 ? set_pops_t<double>(c, comp, f, where, c->pd) : set_pops_t<float>(c, comp, f, where, c->pf);
+}
+
+lbm_status lbm_velocity_set(const lbm_ctx* c, int* q, int* e, double* w)
+{
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (q) *q = c->Q;
+    for (int i = 0; i < c->Q; ++i) {
+        const bool d2 = c->D == 2;
+        if (e) {
+            e[3 * i + 0] = d2 ? D2Q9::ex(i) : D3Q19::ex(i);
+            e[3 * i + 1] = d2 ? D2Q9::ey(i) : D3Q19::ey(i);
+            e[3 * i + 2] = d2 ? D2Q9::ez(i) : D3Q19::ez(i);
+        }
+        if (w) w[i] = d2 ? D2Q9::w(i) : D3Q19::w(i);
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_ctx* c)
+{
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (c->sticky != LBM_OK) return c->sticky;
+    return check_status_word(c);
+}
+
+long long lbm_kernel_launches(const lbm_ctx* c) { return c ? c->launches : 0; }
+
+}  // extern "C"
+
+namespace {
+template <typename T>
+lbm_status profile_t(lbm_ctx* c, int nsteps, double* ms, long long* nl, const Params<T>& P)
+{
+    cudaEvent_t ev[4];
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return fail_cuda(c, cudaErrorUnknown);
+    double acc[3] = {0, 0, 0};
+    long long cnt[3] = {0, 0, 0};
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < nsteps && e == cudaSuccess; ++s) {
+        KArgs<T> a = base_args<T>(c, P);
+        e = cudaEventRecord(ev[0], c->stream);
+        if (e == cudaSuccess) e = dispatch<T>(c, OP_DENSITY, a);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
+        if (e == cudaSuccess && c->n_bsolid > 0) e = dispatch<T>(c, OP_VIRTUAL, a);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2], c->stream);
+        if (e == cudaSuccess) e = dispatch<T>(c, OP_COLLIDE, a);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[3], c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+        if (e != cudaSuccess) break;
+        c->cur ^= 1;
+        float t;
+        for (int k = 0; k < 3; ++k) {
+            if (k == 1 && c->n_bsolid == 0) continue;
+            e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            if (e != cudaSuccess) break;
+            acc[k] += t;
+            cnt[k] += 1;
+        }
+    }
+    for (auto& x : ev) cudaEventDestroy(x);
+    if (e != cudaSuccess) return fail_cuda(c, e);
+    for (int k = 0; k < 3; ++k) {
+        if (ms) ms[k] = acc[k];
+        if (nl) nl[k] = cnt[k];
+    }
+    return check_status_word(c);
+}
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_profile_step(lbm_ctx* c, int nsteps, double* ms, long long* launches)
+{
+    if (!c || nsteps < 0) return LBM_ERR_INVALID_ARG;
+    if (c->sticky != LBM_OK) return c->sticky;
+    if (!ready(c)) return LBM_ERR_STATE;
+    return c->elt == 8 ? profile_t<double>(c, nsteps, ms, launches, c->pd)
+                       : profile_t<float>(c, nsteps, ms, launches, c->pf);
+}
+
+lbm_status lbm_temperature(const lbm_ctx* c, int comp, double* T)
+{
+    if (!c || !T || comp < 0 || comp >= c->prm.ncomp) return LBM_ERR_INVALID_ARG;
+    *T = c->T[comp];
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* c) { delete c; }
+
+const char* lbm_status_str(lbm_status s)
+{
+    switch (s) {
+    case LBM_OK: return "LBM_OK";
+    case LBM_ERR_INVALID_ARG: return "LBM_ERR_INVALID_ARG";
+    case LBM_ERR_WORKSPACE: return "LBM_ERR_WORKSPACE";
+    case LBM_ERR_CUDA: return "LBM_ERR_CUDA";
+    case LBM_ERR_UNSTABLE: return "LBM_ERR_UNSTABLE";
+    case LBM_ERR_TIMEOUT: return "LBM_ERR_TIMEOUT";
+    case LBM_ERR_STATE: return "LBM_ERR_STATE";
+    }
+    return "LBM_ERR_UNKNOWN";
+}
+
+}  // extern "C"

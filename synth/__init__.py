@@ -94,7 +94,7 @@ def droplet_field(shape_xyz, centers, radii, rho_l, rho_g, width, periodic=True)
 def random_droplets(shape_xyz, count, rmin, rmax, width, seed, max_tries=100000):
     """Centres and radii of `count` droplets with radii U[rmin, rmax], placed at
     uniformly random positions in a periodic box by rejection so that any two
-    are separated by at least r_i + r_j + 2 w (minimum image)."""
+    are separated by at least r_i + r_j + w (minimum image)."""
     nx, ny, nz = shape_xyz
     dims = [nx, ny, nz] if nz > 1 else [nx, ny]
     u = uniform(seed, max_tries * 4)
@@ -113,7 +113,7 @@ def random_droplets(shape_xyz, count, rmin, rmax, width, seed, max_tries=100000)
                 dd = abs(c[a] - c2[a])
                 dd = min(dd, dims[a] - dd)
                 d2 += dd * dd
-            if d2 < (r + r2 + 2 * width) ** 2:
+            if d2 < (r + r2 + width) ** 2:
                 ok = False
                 break
         if ok:
@@ -135,7 +135,8 @@ def gaussian_random_field(shape_xyz, corr_length, seed):
     ky = np.fft.fftfreq(ny)[None, :, None]
     kx = np.fft.rfftfreq(nx)[None, None, :]
     k2 = (2 * np.pi) ** 2 * (kx ** 2 + ky ** 2 + kz ** 2)
-    g = np.fft.irfftn(np.fft.rfftn(z) * np.exp(-0.5 * corr_length ** 2 * k2), s=(nz, ny, nx))
+    g = np.fft.irfftn(np.fft.rfftn(z) * np.exp(-0.5 * corr_length ** 2 * k2), s=(nz, ny, nx),
+                      axes=(0, 1, 2))
     g -= g.mean()
     g /= g.std()
     return g

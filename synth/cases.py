@@ -59,6 +59,15 @@ COEX = {
 # bisection on the vapour density of a flat liquid slab (D2Q9, BGK, tau = 1).
 A_STAR = {("CS", 0.7): -0.276, ("CS", 0.8): -0.275, ("PR", 0.6): -0.233, ("PR", 0.8): -0.249}
 
+# Peng-Robinson at T = 0.6 Tc (density ratio 853): the liquid sits close to the
+# repulsive pole 1/b, so the EOS is stiff and droplets blow up with alpha = 1.
+# The pressure scaling alpha^k of Eq. eos_potential keeps the Maxwell pair but
+# widens the interface; alpha = 0.1 with the matching mixing weight (flat-slab
+# bisection as above, interface width 10) is stable in 3-D.
+PR06_ALPHA = 0.1
+PR06_A = -0.3227
+PR06_WIDTH = 10.0
+
 # psi = exp(-1/rho) with g = -10/3: coexistence 0.367528 / 2.78279, ratio 7.57,
 # the ratio of about 7.6 of the paper's performance droplet (Section 5)
 EXP_G = -10.0 / 3.0
@@ -78,7 +87,7 @@ def base_case(lattice, shape, **kw):
     return case
 
 
-def with_eos(case, name, T_red, comps=(0,)):
+def with_eos(case, name, T_red, comps=(0, 1)):
     """Set the EOS (and its paper parameter set) of the given components."""
     c = dict(case)
     for key in ("eos_a", "eos_b", "eos_R", "eos_omega"):
@@ -115,13 +124,13 @@ def droplet_2d_cs(n=128, radius=25.0, width=5.0, real="f64"):
     return case, dict(rho=[rho])
 
 
-def droplets_3d_pr(n=256, count=8, rmin=12.0, rmax=40.0, width=5.0, seed=1234, real="f32",
-                   shape=None, A=A_STAR[("PR", 0.6)]):
+def droplets_3d_pr(n=256, count=8, rmin=12.0, rmax=40.0, width=PR06_WIDTH, seed=1234, real="f32",
+                   shape=None, A=PR06_A, alpha=PR06_ALPHA):
     """D3Q19 single-component Shan-Chen, Peng-Robinson (a = 2/49, b = 2/21, R = 1,
     omega = 0.344, T = 0.6 Tc), MRT, periodic cube, `count` droplets with seeded
     radii U[rmin, rmax] at random non-overlapping centres."""
     shape = tuple(shape) if shape is not None else (n, n, n)
-    case = base_case("D3Q19", shape, real=real, collision="MRT", A=[A, A])
+    case = base_case("D3Q19", shape, real=real, collision="MRT", A=[A, A], alpha=[alpha, alpha])
     case = with_eos(case, "PR", 0.6)
     rg, rl = COEX[("PR", 0.6)]
     centers, radii = random_droplets(shape, count, rmin, rmax, width, seed)

@@ -1,0 +1,326 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Same seeded inputs on both sides; fields are compared with the relative
+L-infinity norm max|a - b| / max|b| per field (density and each velocity
+component). Tolerances: FP32 <= 1e-5 after 100 steps and <= 1e-3 after 5000
+steps; FP64 <= 1e-10.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import cases, droplet_field, random_droplets, random_field, random_solids
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_17713_gb300.build import build
+    build()
+
+
+def rel_linf(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    scale = np.abs(b).max()
+    return np.abs(a - b).max() / (scale if scale > 0 else 1.0)
+
+
+def run_both(case, rhos, steps, solid=None, us=None):
+    from paper_2506_17713_gb300 import Lattice
+    lat = Lattice(case)
+    orc = oracle.OracleSim(case)
+    if solid is not None:
+        lat.set_geometry(solid)
+        orc.set_geometry(solid)
+    for k, r in enumerate(rhos):
+        u = None if us is None else us[k]
+        lat.init_fields(k, r, u)
+        orc.init_fields(k, r, u)
+    lat.step(steps)
+    orc.step(steps)
+    return lat, orc
+
+
+def compare(lat, orc, tol, comps=None):
+    comps = list(range(lat.K)) if comps is None else comps
+    if lat.K > 1:
+        comps = comps + [-1]
+    worst = 0.0
+    for k in comps:
+        rg, ug = lat.macroscopic_host(k)
+        ro, uo = orc.macroscopic(k)
+        assert np.isfinite(rg).all() and np.isfinite(ug).all()
+        e = [rel_linf(rg, ro)] + [rel_linf(ug[d], uo[d]) for d in range(lat.D)]
+        worst = max(worst, max(e))
+        assert max(e) <= tol, (k, e)
+    return worst
+
+
+def droplet_case(shape, seed=3, count=1, rmin=9.0, rmax=11.0, real="f32"):
+    case, init = cases.droplets_3d_pr(shape=shape, count=count, rmin=rmin, rmax=rmax, seed=seed,
+                                      real=real)
+    return case, init["rho"]
+
+
+# ---------------------------------------------------------------------------
+# a1-a7: the full step on the paper's configurations
+# ---------------------------------------------------------------------------
+
+def test_d2q9_cs_droplet_fp64_full_config():
+    # 128^2 periodic, CS a = 0.5, b = 4, T = 0.7 Tc, BGK tau = 1, R = 25, w = 5, 2000 steps
+    case, init = cases.droplet_2d_cs()
+    lat, orc = run_both(case, init["rho"], 2000)
+    compare(lat, orc, 1e-10)
+    m, p = lat.diagnostics()
+    mo, po = orc.diagnostics()
+    assert abs(m[0] - mo[0]) < 1e-10 * mo[0]
+
+
+def test_d3q19_pr_mrt_fp32_100_steps_ragged():
+    case, rho = droplet_case((70, 37, 29), count=1)
+    lat, orc = run_both(case, rho, 100)
+    compare(lat, orc, 1e-5)
+
+
+def test_d3q19_pr_mrt_fp32_5000_steps():
+    case, rho = droplet_case((40, 36, 34), count=1, rmin=10.0, rmax=10.0)
+    lat, orc = run_both(case, rho, 5000)
+    compare(lat, orc, 1e-3)
+
+
+def test_d3q19_pr_mrt_fp64_matches_tightly():
+    case, rho = droplet_case((33, 30, 27), real="f64")
+    lat, orc = run_both(case, rho, 60)
+    compare(lat, orc, 1e-10)
+
+
+def test_paper_performance_case_exp_bgk():
+    # psi = exp(-1/rho), D3Q19 BGK, droplet in its vapour (Section 5 shape, reduced)
+    case, init = cases.droplet_3d_exp(shape=(48, 40, 36), radius=12.0)
+    lat, orc = run_both(case, init["rho"], 100)
+    compare(lat, orc, 1e-5)
+
+
+@pytest.mark.parametrize("eos,Tr", [("CS", 0.7), ("VdW", 0.8), ("RK", 0.8), ("RKS", 0.8), ("PR", 0.8)])
+def test_every_eos_d2q9(eos, Tr):
+    shape = (45, 38, 1)
+    case = cases.base_case("D2Q9", shape, collision="MRT", A=[-0.25, -0.25], real="f64")
+    case = cases.with_eos(case, eos, Tr)
+    p = cases.EOS_PARAMS[eos]
+    rg, rl, _ = oracle.maxwell(eos, p["eos_a"], p["eos_b"], 1.0, p["eos_omega"], Tr)
+    rho = droplet_field(shape, [(20.0, 17.0)], [9.0], rl, rg, 5.0)
+    lat, orc = run_both(case, [rho], 200)
+    compare(lat, orc, 1e-10)
+    T = lat.temperature(0)
+    Tc = oracle.eos_Tc(eos, p["eos_a"], p["eos_b"], 1.0)
+    assert abs(T / (Tr * Tc) - 1) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# a2 wetting, a4 cross-component force, a7 bounce-back, a8 constant-density faces
+# ---------------------------------------------------------------------------
+
+def _two_component(shape, real="f32", **kw):
+    case = cases.base_case("D3Q19", shape, ncomp=2, collision="MRT", psi=["rho", "rho"],
+                           g=[[-0.01, 0.19], [0.19, -0.01]], tau=[1.0, 0.7], real=real,
+                           wet_phi=[1.2, 1.0], wet_drho=[0.0, 0.05], rho_lo=[0.02, 0.02],
+                           rho_hi=[1.2, 1.2], accel=[[2e-5, 0, 0], [1e-5, 0, 0]])
+    case.update(kw)
+    nx, ny, nz = shape
+    x = np.arange(nx)[None, None, :] * np.ones((nz, ny, 1))
+    r1 = np.where(x < nx // 2, 1.0, 0.03) + 0.01 * random_field(shape, -1, 1, 41)
+    r2 = np.where(x < nx // 2, 0.03, 1.0) + 0.01 * random_field(shape, -1, 1, 42)
+    return case, [r1, r2]
+
+
+def test_two_component_solids_wetting_mrt():
+    shape = (37, 29, 23)
+    case, rhos = _two_component(shape, bc=["periodic", "periodic", "wall", "wall", "periodic", "periodic"])
+    solid = random_solids(shape, 0.12, 51)
+    lat, orc = run_both(case, rhos, 100, solid=solid)
+    compare(lat, orc, 1e-5)
+
+
+def test_two_component_common_velocity_bgk_fp64():
+    shape = (21, 17, 13)
+    case, rhos = _two_component(shape, real="f64", collision="BGK", velocity="common")
+    solid = random_solids(shape, 0.1, 52)
+    lat, orc = run_both(case, rhos, 80, solid=solid)
+    compare(lat, orc, 1e-10)
+
+
+def test_pressure_faces_two_component_porous():
+    shape = (40, 18, 16)
+    case, init = cases.porous_two_component(shape=shape, porosity=0.6, corr_length=3.0, buffer=4)
+    case["collision"] = "MRT"
+    lat, orc = run_both(case, init["rho"], 100, solid=init["solid"])
+    compare(lat, orc, 1e-5)
+
+
+def test_d2q9_walls_body_force_fp32():
+    shape = (64, 33, 1)
+    case = cases.base_case("D2Q9", shape, collision="MRT", psi=["exp"], g=[[cases.EXP_G, 0], [0, cases.EXP_G]],
+                           accel=[[1e-5, -2e-6, 0], [0, 0, 0]], wet_phi=[1.1, 1.1], rho_lo=[0.3, 0.3],
+                           rho_hi=[3.0, 3.0],
+                           bc=["periodic", "periodic", "wall", "wall", "periodic", "periodic"])
+    rg, rl = cases.EXP_COEX
+    rho = droplet_field(shape, [(32.0, 10.0)], [9.0], rl, rg, 4.0, periodic=False)
+    solid = np.zeros((1, 33, 64), dtype=np.uint8)
+    solid[0, 0, :] = 1
+    solid[0, 20:24, 40:44] = 1
+    lat, orc = run_both(case, [rho], 300, solid=solid)
+    compare(lat, orc, 1e-5)
+
+
+def test_virtual_density_values_at_solids():
+    # psi at boundary solids is the same on both sides: compared through the
+    # force-driven velocity next to the wall after one step
+    shape = (24, 20, 18)
+    case = cases.base_case("D3Q19", shape, psi=["exp"], g=[[cases.EXP_G, 0], [0, cases.EXP_G]],
+                           wet_phi=[1.3, 1.3], rho_lo=[0.3, 0.3], rho_hi=[2.0, 2.0])
+    solid = np.zeros((18, 20, 24), dtype=np.uint8)
+    solid[:, 5:9, :] = 1
+    rho = random_field(shape, 0.5, 1.5, 61)
+    lat, orc = run_both(case, [rho], 1, solid=solid)
+    compare(lat, orc, 1e-6)
+
+
+# ---------------------------------------------------------------------------
+# Edge cases
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape,lattice", [((1, 6, 1), "D2Q9"), ((5, 1, 4), "D3Q19"), ((3, 2, 1), "D3Q19"),
+                                            ((33, 1, 1), "D2Q9")])
+def test_degenerate_shapes(shape, lattice):
+    case = cases.base_case(lattice, shape, psi=["exp"], g=[[cases.EXP_G, 0], [0, cases.EXP_G]], real="f64",
+                           collision="MRT")
+    rho = random_field(shape, 0.5, 2.0, 71)
+    lat, orc = run_both(case, [rho], 25)
+    compare(lat, orc, 1e-10)
+
+
+def test_almost_all_solid():
+    shape = (6, 5, 4)
+    solid = np.ones((4, 5, 6), dtype=np.uint8)
+    solid[2, 2, 3] = 0
+    solid[2, 2, 4] = 0
+    case = cases.base_case("D3Q19", shape, psi=["exp"], g=[[cases.EXP_G, 0], [0, cases.EXP_G]], real="f64")
+    rho = random_field(shape, 0.5, 2.0, 72)
+    lat, orc = run_both(case, [rho], 10, solid=solid)
+    compare(lat, orc, 1e-10)
+    m, _ = lat.diagnostics()
+    assert abs(m[0] - rho[2, 2, 3] - rho[2, 2, 4]) < 1e-12
+
+
+def test_rest_state_stays_at_rest():
+    shape = (20, 18, 16)
+    case = cases.droplets_3d_pr(shape=shape, count=1, rmin=3, rmax=3)[0]
+    from paper_2506_17713_gb300 import Lattice
+    lat = Lattice(case)
+    lat.init_fields(0, np.full((16, 18, 20), 5.0))
+    lat.step(50)
+    r, u = lat.macroscopic_host(0)
+    assert np.abs(r - 5.0).max() < 5.0 * 1e-6
+    assert np.abs(u).max() < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Checkpoint, determinism, diagnostics (a9, a10)
+# ---------------------------------------------------------------------------
+
+def test_populations_match_oracle_and_roundtrip_bitwise():
+    import torch
+    from paper_2506_17713_gb300 import Lattice
+    shape = (23, 19, 17)
+    case, rhos = _two_component(shape)
+    solid = random_solids(shape, 0.1, 81)
+    lat, orc = run_both(case, rhos, 30, solid=solid)
+    e_gpu, _ = lat.velocity_set()
+    perm = [next(j for j in range(orc.Q) if tuple(orc.e[j]) == tuple(e_gpu[i])) for i in range(lat.Q)]
+    for k in range(2):
+        fg = lat.populations(k).cpu().numpy()
+        fo = orc.populations(k)[perm]
+        assert rel_linf(fg, fo) < 1e-5
+    # get -> set into a fresh lattice -> both continue identically (bit for bit)
+    other = Lattice(case)
+    other.set_geometry(solid)
+    for k in range(2):
+        other.set_populations(k, lat.populations(k))
+        assert torch.equal(other.populations(k), lat.populations(k))
+    lat.step(20)
+    other.step(20)
+    for k in range(2):
+        assert torch.equal(other.populations(k), lat.populations(k))
+
+
+def test_deterministic_reruns():
+    import torch
+    from paper_2506_17713_gb300 import Lattice
+    case, rho = droplet_case((48, 40, 36), count=1)
+    outs = []
+    for _ in range(2):
+        lat = Lattice(case)
+        lat.init_fields(0, rho[0])
+        lat.step(40)
+        r, u = lat.macroscopic(0)
+        m, p = lat.diagnostics()
+        outs.append((r, u, m, p))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][2], outs[1][2]) and np.array_equal(outs[0][3], outs[1][3])
+
+
+def test_diagnostics_mass_momentum_and_residual():
+    case, rho = droplet_case((40, 36, 32), count=1, real="f64")
+    lat, orc = run_both(case, rho, 50)
+    m, p = lat.diagnostics()
+    mo, po = orc.diagnostics()
+    assert abs(m[0] / mo[0] - 1) < 1e-12
+    assert np.abs(p - po).max() < 1e-9 * mo[0]
+    _, _, r0 = lat.diagnostics(residual=True)
+    assert r0 == 1.0
+    lat.step(10)
+    _, _, r1 = lat.diagnostics(residual=True)
+    assert 0.0 < r1 < 1.0
+
+
+def test_mass_conserved_fp32_1000_steps():
+    case, rho = droplet_case((48, 44, 40), count=1)
+    from paper_2506_17713_gb300 import Lattice
+    lat = Lattice(case)
+    lat.init_fields(0, rho[0])
+    m0, _ = lat.diagnostics()
+    lat.step(1000)
+    m1, _ = lat.diagnostics()
+    assert abs(m1[0] / m0[0] - 1) < 1e-5
+
+
+def test_unstable_run_reports_error_and_sticks():
+    # a liquid far above the EOS stability range blows up; the status is sticky
+    from paper_2506_17713_gb300 import Lattice, LbmError
+    shape = (16, 16, 16)
+    case = cases.droplets_3d_pr(shape=shape, count=1, rmin=3, rmax=3, alpha=1.0, A=0.0, width=2.0)[0]
+    rg, rl = cases.COEX[("PR", 0.6)]
+    rho = droplet_field(shape, [(8.0, 8.0, 8.0)], [5.0], rl, rg, 2.0)
+    lat = Lattice(case)
+    lat.init_fields(0, rho)
+    lat.step(200)
+    with pytest.raises(LbmError) as ei:
+        lat.diagnostics()
+    assert ei.value.status == 4
+    with pytest.raises(LbmError):
+        lat.step(1)
+
+
+# ---------------------------------------------------------------------------
+# Full size, launch configuration of the benchmark
+# ---------------------------------------------------------------------------
+
+def test_full_size_256_cubed_two_steps():
+    case, init = cases.droplets_3d_pr()
+    lat, orc = run_both(case, init["rho"], 2)
+    compare(lat, orc, 1e-5)
