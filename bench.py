@@ -31,29 +31,27 @@ WORKLOADS = {
 }
 
 
-def make_case(name):
+def make_case(name, n=256):
     from synth import cases
     if name == "pr256":
-        case, init = cases.droplets_3d_pr(n=256)
+        case, init = cases.droplets_3d_pr(n=n)
     elif name == "exp256":
-        case, init = cases.droplet_3d_exp(n=256)
+        case, init = cases.droplet_3d_exp(n=n, radius=30.0 * n / 256)
     else:
         raise SystemExit("unknown workload " + name)
     return case, init
 
 
 def algorithmic_bytes(case):
-    """Bytes each kernel must move per lattice update (DRAM, once per value):
-    collide: read K*Q populations + psi (+ U) [+ mask], write K*Q populations;
-    density: read K*Q populations [+ mask], write psi (+ U) [+ rho]."""
+    """Bytes each kernel must move per lattice update (DRAM, each value once):
+    collide: read K*Q populations + K psi [+ 1 B mask], write K*Q populations;
+    density: read K*Q populations [+ 1 B mask], write K psi [+ K rho next to solids]."""
     Q = 19 if case["lattice"] == "D3Q19" else 9
     e = 8 if case.get("real") == "f64" else 4
     K = int(case.get("ncomp", 1))
-    needs_U = any(float(a) != 0.0 for a in case.get("A", [0.0])[:K])
     geom = any(b != "periodic" for b in case.get("bc", ["periodic"] * 6))
-    scal = K * e * (2 if needs_U else 1)
-    collide = 2 * K * Q * e + scal + (1 if geom else 0)
-    density = K * Q * e + scal + (K * e if geom else 0) + (1 if geom else 0)
+    collide = 2 * K * Q * e + K * e + (1 if geom else 0)
+    density = K * Q * e + K * e + (K * e + 1 if geom else 0)
     return {"collide": collide, "density": density, "step": collide + density}
 
 
@@ -173,7 +171,7 @@ def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
         return
-    case, init = make_case(args.workload)
+    case, init = make_case(args.workload, args.n)
     steps = max(1, min(args.steps, args.ref_steps))
     mlups_w, _, _ = oracle_sample(case, init, 1)                 # warm-up (page-in)
     mlups, dt, threads = oracle_sample(case, init, steps)
@@ -203,7 +201,7 @@ def run_ours(args):
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    case, init = make_case(args.workload)
+    case, init = make_case(args.workload, args.n)
     nx, ny, nz = case["shape"]
     K = int(case.get("ncomp", 1))
     N = nx * ny * nz
@@ -285,7 +283,8 @@ def run_ours(args):
         "ms_per_step": round(1e3 * secs_max / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if case.get("real") != "f64" else "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "shape": [nx, ny, nz], "components": K,
+        "config": {"workload": WORKLOADS[args.workload] if args.n == 256 else
+                   WORKLOADS[args.workload].replace("256^3", "%d^3" % args.n), "shape": [nx, ny, nz], "components": K,
                    "parallelism": "replicas" if world > 1 else "single-gpu",
                    "l2": "inputs larger than L2 (two %.2f GB population buffers)" % (
                        K * 19 * N * 4 / 1e9)},
@@ -316,6 +315,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="pr256", choices=sorted(WORKLOADS))
+    ap.add_argument("--n", type=int, default=256, help="cube edge (256 = the benchmark workload; "
+                    "smaller edges are for profiling captures)")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--ref-steps", type=int, default=3)

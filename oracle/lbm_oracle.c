@@ -23,7 +23,7 @@
  * Readings of the paper taken where it is silent (same readings as the CUDA path):
  *   G_i = w_i / c_s^2 on all Q-1 links (so sum_i G_i e_i e_i = I);
  *   U^k = alpha p_EOS - c_s^2 rho for the EOS pseudopotential, U = g_kk psi^2/2 otherwise;
- *   psi = sqrt(max(0, 2 U / g_kk)) (argument clamped at zero);
+ *   psi = sqrt(max(0, 2 U / g_kk)) (argument clamped at zero, and U = 0 there);
  *   equilibrium velocity = bare sum_i f_i e_i / rho (per component, or the
  *   common Shan-Chen velocity when requested); EDM shift dU = F / rho;
  *   output velocity (sum_i f_i e_i + F/2) / rho;
@@ -203,7 +203,9 @@ static void psi_of_rho(const orc_params* p, const double* T, const double* alpha
         double pe = eos_p_T(p->eos[k], p->eos_a[k], p->eos_b[k], p->eos_R[k], T[k], alphaT[k], rho);
         double u = p->alpha[k] * pe - CS2 * rho;
         double arg = 2.0 * u / gkk;
-        *U = u;
+        /* psi is real only where 2U/g >= 0; elsewhere psi = 0 and, keeping
+         * U = g psi^2 / 2 as everywhere else, U = 0 */
+        *U = arg > 0.0 ? u : 0.0;
         *psi = sqrt(arg > 0.0 ? arg : 0.0);
     } else {
         double s = p->psi_kind[k] == ORC_PSI_RHO ? rho : exp(-1.0 / rho);

@@ -23,14 +23,15 @@ struct Params {
     int ncomp;
     int collision;
     int common_velocity;
-    int needs_U;         // some component mixes in the Zhang-Chen force (A != 0)
     int bc[6];
     int psi_kind[2];
     int eos[2];
     T omega[2];          // 1 / tau
     T rates[2][19];      // MRT rates, stress = 1/tau, conserved = 0
     T eos_a[2], eos_b[2], RT[2], alphaT[2], sqrtT[2];
+    T eos_b_lo[2], RT_lo[2], att[2], att_lo[2], alpha_lo[2];  // hi + lo parts for FP32
     T alpha[2], A[2], g[2][2];
+    T oneA[2], oneA_lo[2];   // 1 - A as hi + lo
     T wet_phi[2], wet_drho[2], rho_min[2], rho_max[2];
     T accel[2][3];
     T bc_rho[2][2];      // [x side][component]
@@ -54,7 +55,6 @@ struct KArgs {
     const T* f_src;      // pre-stream (post-collision) populations, [K][Q][N]
     T* f_dst;            // next pre-stream buffer
     T* psi;              // [K][N]
-    T* U;                // [K][N]
     T* rho;              // [K][N] (read by the virtual-density pass)
     const uint8_t* solid;
     const int* bsolid;   // boundary-solid node list

@@ -24,14 +24,88 @@
 #include "args.h"
 #include "lattice.cuh"
 
+// Per-node arithmetic is __host__ __device__ so that host-side harnesses can
+// exercise exactly the arithmetic of the kernels.
+#define LBM_HD __host__ __device__ __forceinline__
+
 namespace lbm {
+
+// Double-float ("float-float") arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2.
+// Error-free transformations (Knuth's TwoSum, FMA-based TwoProd) give about 44
+// significant bits from FP32 operations. Used where FP32 rounding would be
+// amplified by the interface dynamics (interaction force, EOS). For T = double
+// the same interface degrades to plain double arithmetic.
+template <typename T>
+struct FF {
+    T hi, lo;
+};
+template <typename T>
+LBM_HD FF<T> ff_two_sum(T a, T b)
+{
+    const T s = a + b;
+    const T bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+template <typename T>
+LBM_HD FF<T> ff_two_prod(T a, T b)
+{
+    const T p = a * b;
+    return {p, fma(a, b, -p)};
+}
+template <typename T>
+LBM_HD FF<T> ff_add(FF<T> a, FF<T> b)
+{
+    FF<T> s = ff_two_sum(a.hi, b.hi);
+    s.lo += a.lo + b.lo;
+    return ff_two_sum(s.hi, s.lo);
+}
+template <typename T>
+LBM_HD FF<T> ff_mul(FF<T> a, FF<T> b)
+{
+    FF<T> p = ff_two_prod(a.hi, b.hi);
+    p.lo = fma(a.hi, b.lo, fma(a.lo, b.hi, p.lo));
+    return ff_two_sum(p.hi, p.lo);
+}
+template <typename T>
+LBM_HD FF<T> ff_mul(FF<T> a, T b)
+{
+    FF<T> p = ff_two_prod(a.hi, b);
+    p.lo = fma(a.lo, b, p.lo);
+    return ff_two_sum(p.hi, p.lo);
+}
+template <typename T>
+LBM_HD FF<T> ff_div(FF<T> a, FF<T> b)
+{
+    const T q1 = a.hi / b.hi;
+    const FF<T> r = ff_add(a, ff_mul(b, -q1));
+    const T q2 = r.hi / b.hi;
+    return ff_two_sum(q1, q2);
+}
+template <typename T>
+LBM_HD FF<T> ff_of(T a) { return {a, T(0)}; }
+
+// Compensated summation (Neumaier's variant of Kahan summation): the running
+// sum carries the rounding error of every addition in a second register, so
+// rho = sum_i f_i and j = sum_i f_i e_i come out within about one rounding of
+// the exact sums of the stored values.
+template <typename T>
+struct CSum {
+    T s = T(0), c = T(0);
+    LBM_HD void add(T v)
+    {
+        const T t = s + v;
+        c += (fabs(s) >= fabs(v)) ? ((s - t) + v) : ((v - t) + s);
+        s = t;
+    }
+    LBM_HD T value() const { return s + c; }
+};
 
 // ---------------------------------------------------------------------------
 // Equation of state and pseudopotential (Section 2.2, Eq. eos_potential)
 // ---------------------------------------------------------------------------
 
 template <typename T>
-__device__ __forceinline__ T eos_pressure(const Params<T>& P, int k, T rho)
+LBM_HD T eos_pressure(const Params<T>& P, int k, T rho)
 {
     const T a = P.eos_a[k], b = P.eos_b[k], RT = P.RT[k];
     switch (P.eos[k]) {
@@ -52,12 +126,64 @@ __device__ __forceinline__ T eos_pressure(const Params<T>& P, int k, T rho)
     }
 }
 
-// psi^k and U^k from rho^k; returns true when the square-root argument was clamped
+// p_EOS(rho) in double-float arithmetic (FP32 storage types): in a stiff liquid
+// the repulsive and attractive terms are large and nearly cancel, so plain FP32
+// loses several bits of the pressure. p = R T rho r(rho) - att rho^2 / D(rho),
+// with the per-EOS factors r, D of the paper's equations of state and att = a
+// alpha(T) (a / sqrt(T) for Redlich-Kwong); parameters are carried as hi + lo.
 template <typename T>
-__device__ __forceinline__ bool pseudopotential(const Params<T>& P, int k, T rho, T& psi, T& U)
+LBM_HD FF<T> eos_pressure_ff(const Params<T>& P, int k, T rho)
+{
+    const FF<T> one = ff_of(T(1));
+    const FF<T> b = {P.eos_b[k], P.eos_b_lo[k]};
+    const FF<T> br = ff_mul(b, rho);
+    FF<T> rep;  // rho r(rho)
+    FF<T> den = one;
+    switch (P.eos[k]) {
+    case EOS_CS: {
+        const FF<T> eta = ff_mul(br, T(0.25));
+        const FF<T> om = ff_add(one, FF<T>{-eta.hi, -eta.lo});
+        // 1 + eta + eta^2 - eta^3 = 1 + eta (1 + eta (1 - eta))
+        const FF<T> num = ff_add(one, ff_mul(eta, ff_add(one, ff_mul(eta, om))));
+        rep = ff_div(ff_mul(num, rho), ff_mul(ff_mul(om, om), om));
+        break;
+    }
+    default: {
+        rep = ff_div(ff_of(rho), ff_add(one, FF<T>{-br.hi, -br.lo}));
+        if (P.eos[k] == EOS_PR) den = ff_add(one, ff_mul(br, ff_add(ff_of(T(2)), FF<T>{-br.hi, -br.lo})));
+        else if (P.eos[k] == EOS_RK || P.eos[k] == EOS_RKS) den = ff_add(one, br);
+        break;
+    }
+    }
+    const FF<T> t1 = ff_mul(rep, FF<T>{P.RT[k], P.RT_lo[k]});
+    const FF<T> t2 = ff_div(ff_mul(ff_two_prod(rho, rho), FF<T>{P.att[k], P.att_lo[k]}), den);
+    return ff_add(t1, FF<T>{-t2.hi, -t2.lo});
+}
+
+// psi^k (and the pseudopotential energy U^k = alpha p_EOS - c_s^2 rho) from rho^k.
+// Returns true when the square-root argument 2U/g was negative (psi clamped to 0).
+template <typename T>
+LBM_HD bool pseudopotential(const Params<T>& P, int k, T rho, T& psi, T& U)
 {
     const T g = P.g[k][k];
     if (P.psi_kind[k] == PSI_EOS) {
+        if (sizeof(T) == 4) {
+            const FF<T> pe = eos_pressure_ff(P, k, rho);
+            const FF<T> third = {T(1.0 / 3.0), T(1.0 / 3.0 - (double)T(1.0 / 3.0))};
+            const FF<T> u = ff_add(ff_mul(pe, FF<T>{P.alpha[k], P.alpha_lo[k]}),
+                                   FF<T>{-ff_mul(third, rho).hi, -ff_mul(third, rho).lo});
+            const FF<T> arg = ff_div(ff_mul(u, T(2)), ff_of(g));
+            U = u.hi + u.lo;
+            if (arg.hi <= T(0)) {
+                psi = T(0);
+                return arg.hi < T(0);
+            }
+            // sqrt of hi + lo: one Newton correction of the FP32 root
+            const T r = sqrt(arg.hi);
+            const FF<T> r2 = ff_two_prod(r, r);
+            psi = r + ((arg.hi - r2.hi) - r2.lo + arg.lo) / (T(2) * r);
+            return false;
+        }
         U = P.alpha[k] * eos_pressure(P, k, rho) - rho * T(1.0 / 3.0);
         const T arg = T(2) * U / g;
         psi = sqrt(arg > T(0) ? arg : T(0));
@@ -89,7 +215,7 @@ __device__ __forceinline__ bool node_of_thread(int nx, int ny, Node& nd)
 // Stencil neighbour x + e for the force and wetting stencils: periodic faces
 // wrap, other faces clamp the coordinate into the domain.
 template <bool GEOM, typename T>
-__device__ __forceinline__ long long stencil_nb(const Params<T>& P, int x, int y, int z, int ex, int ey,
+LBM_HD long long stencil_nb(const Params<T>& P, int x, int y, int z, int ex, int ey,
                                                 int ez)
 {
     int a = x + ex, b = y + ey, c = z + ez;
@@ -105,7 +231,7 @@ __device__ __forceinline__ long long stencil_nb(const Params<T>& P, int x, int y
 // Pull-stream source of direction (ex, ey, ez) at node (x, y, z).
 // Returns 0 = regular source *src, 1 = bounce back, 2 = unknown (constant-density face).
 template <bool GEOM, typename T>
-__device__ __forceinline__ int pull_source(const Params<T>& P, const uint8_t* __restrict__ solid, int x,
+LBM_HD int pull_source(const Params<T>& P, const uint8_t* __restrict__ solid, int x,
                                            int y, int z, int ex, int ey, int ez, long long& src)
 {
     int a = x - ex, b = y - ey, c = z - ez;
@@ -147,7 +273,7 @@ __device__ __forceinline__ int pull_source(const Params<T>& P, const uint8_t* __
 //   rho u_n = rho_b - (sum_{e_x = 0} f + 2 sum_{nin e_x < 0} f)
 //   f_i = f_opp(i) + 6 w_i rho u_n - (e_iy N_y + e_iz N_z) / 2,  N_t = sum_{e_x = 0} f e_t
 template <class L, typename T>
-__device__ __forceinline__ void zou_he(T (&f)[L::Q], int nin, T rho_b)
+LBM_HD void zou_he(T (&f)[L::Q], int nin, T rho_b)
 {
     T s0 = T(0), sneg = T(0), Ny = T(0), Nz = T(0);
 #pragma unroll
@@ -176,7 +302,7 @@ __device__ __forceinline__ void zou_he(T (&f)[L::Q], int nin, T rho_b)
 // Post-stream populations of component k at a fluid node (pull + bounce-back +
 // constant-density faces).
 template <class L, typename T, bool GEOM>
-__device__ __forceinline__ void gather_k(const T* __restrict__ f_all, const Params<T>& P,
+LBM_HD void gather_k(const T* __restrict__ f_all, const Params<T>& P,
                                          const uint8_t* __restrict__ solid, const Node& nd, int k,
                                          T (&f)[L::Q])
 {
@@ -197,80 +323,100 @@ __device__ __forceinline__ void gather_k(const T* __restrict__ f_all, const Para
 }
 
 template <class L, typename T>
-__device__ __forceinline__ void moments(const T (&f)[L::Q], T& rho, T (&j)[3])
+LBM_HD T density(const T (&f)[L::Q])
 {
-    T r = T(0), jx = T(0), jy = T(0), jz = T(0);
+    CSum<T> r;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) r.add(f[i]);
+    return r.value();
+}
+
+template <class L, typename T>
+LBM_HD void moments(const T (&f)[L::Q], T& rho, T (&j)[3])
+{
+    CSum<T> jx, jy, jz;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        r += f[i];
-        if (L::ex(i)) jx += L::ex(i) > 0 ? f[i] : -f[i];
-        if (L::ey(i)) jy += L::ey(i) > 0 ? f[i] : -f[i];
-        if (L::ez(i)) jz += L::ez(i) > 0 ? f[i] : -f[i];
+        if (L::ex(i)) jx.add(L::ex(i) > 0 ? f[i] : -f[i]);
+        if (L::ey(i)) jy.add(L::ey(i) > 0 ? f[i] : -f[i]);
+        if (L::ez(i)) jz.add(L::ez(i) > 0 ? f[i] : -f[i]);
     }
-    rho = r;
-    j[0] = jx;
-    j[1] = jy;
-    j[2] = jz;
+    rho = density<L, T>(f);
+    j[0] = jx.value();
+    j[1] = jy.value();
+    j[2] = jz.value();
 }
 
 // ---------------------------------------------------------------------------
 // Interaction force (Eq. software_ff_force_mcmp), G_i = w_i / c_s^2
 // ---------------------------------------------------------------------------
 
+// G_i = w_i / c_s^2 is c_i / 12 with integer c_i (D3Q19: 2 on axis links, 1 on
+// edge links; D2Q9: 4 and 1), so the stencil sums integer multiples of neighbour
+// differences with compensated summation and scales by 1/12 once. In FP32 this
+// keeps the force within about one rounding of its exact value; the force feeds
+// the velocity shift F / rho every step, where larger errors grow quickly.
+template <class L>
+LBM_HD constexpr int g_twelfths(int i)
+{
+    return (int)(36.0 * L::w(i) + 0.5);  // 12 * 3 w_i
+}
+
 template <class L, typename T, int K, bool GEOM>
-__device__ __forceinline__ void interaction_force(const KArgs<T>& a, const Node& nd, const T (&rho)[K],
-                                                  T (&F)[K][3])
+LBM_HD void interaction_force(const KArgs<T>& a, const Node& nd, const T (&rho)[K], T (&F)[K][3])
 {
     const Params<T>& P = a.p;
     const long long N = P.N;
-    T sc[K][3], zc[K][3];
+    FF<T> acc[K][3];
+    FF<T> px[K];
+    T hA[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k)
+    for (int k = 0; k < K; ++k) {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) sc[k][d] = zc[k][d] = T(0);
-    const bool useU = P.needs_U != 0;
-    // opposite pairs (i, opp(i)) with i the odd member: accumulate G_i (v_i - v_opp) e_i
+        for (int d = 0; d < 3; ++d) acc[k][d] = ff_of(T(0));
+        // (1 - A_k) psi^k(x), with 1 - A_k carried as hi + lo
+        px[k] = ff_mul(FF<T>{P.oneA[k], P.oneA_lo[k]}, a.psi[(long long)k * N + nd.n]);
+        hA[k] = T(0.5) * P.A[k];
+    }
+    // pair (i, opp(i)): c_i e_i sum_k' g_kk' (psi1 - psi2)^k' [(1-A_k) psi^k(x) + [k'=k] A_k (psi1 + psi2)^k / 2]
 #pragma unroll
     for (int i = 1; i < L::Q; ++i) {
         if (L::opp(i) < i) continue;
         const int o = L::opp(i);
         const long long m1 = stencil_nb<GEOM>(P, nd.x, nd.y, nd.z, L::ex(i), L::ey(i), L::ez(i));
         const long long m2 = stencil_nb<GEOM>(P, nd.x, nd.y, nd.z, L::ex(o), L::ey(o), L::ez(o));
-        T ps1[K], ps2[K];
+        const T c = T(g_twelfths<L>(i));
+        T p1[K], p2[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            ps1[k] = a.psi[(long long)k * N + m1];
-            ps2[k] = a.psi[(long long)k * N + m2];
+            p1[k] = a.psi[(long long)k * N + m1];
+            p2[k] = a.psi[(long long)k * N + m2];
         }
-        const T G = T(3.0 * L::w(i));
+        FF<T> dpsi[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) dpsi[k] = ff_two_sum(p1[k], -p2[k]);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            T d = T(0);
+            FF<T> t = ff_of(T(0));
 #pragma unroll
-            for (int kp = 0; kp < K; ++kp) d += P.g[k][kp] * (ps1[kp] - ps2[kp]);
-            const T gd = G * d;
-            if (L::ex(i)) sc[k][0] += L::ex(i) > 0 ? gd : -gd;
-            if (L::ey(i)) sc[k][1] += L::ey(i) > 0 ? gd : -gd;
-            if (L::ez(i)) sc[k][2] += L::ez(i) > 0 ? gd : -gd;
-            if (useU) {
-                const T du = G * (a.U[(long long)k * N + m1] - a.U[(long long)k * N + m2]);
-                if (L::ex(i)) zc[k][0] += L::ex(i) > 0 ? du : -du;
-                if (L::ey(i)) zc[k][1] += L::ey(i) > 0 ? du : -du;
-                if (L::ez(i)) zc[k][2] += L::ez(i) > 0 ? du : -du;
+            for (int kp = 0; kp < K; ++kp) {
+                FF<T> w = px[k];
+                if (kp == k) w = ff_add(w, ff_mul(ff_two_sum(p1[k], p2[k]), hA[k]));
+                t = ff_add(t, ff_mul(ff_mul(dpsi[kp], w), P.g[k][kp] * c));
             }
+            if (L::ex(i)) acc[k][0] = ff_add(acc[k][0], L::ex(i) > 0 ? t : FF<T>{-t.hi, -t.lo});
+            if (L::ey(i)) acc[k][1] = ff_add(acc[k][1], L::ey(i) > 0 ? t : FF<T>{-t.hi, -t.lo});
+            if (L::ez(i)) acc[k][2] = ff_add(acc[k][2], L::ez(i) > 0 ? t : FF<T>{-t.hi, -t.lo});
         }
     }
+    const FF<T> m12 = {T(-1.0 / 12.0), T(-1.0 / 12.0 - (double)T(-1.0 / 12.0))};
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const T pk = a.psi[(long long)k * N + nd.n];
-        const T Ak = P.A[k];
+    for (int k = 0; k < K; ++k)
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            T v = (T(1) - Ak) * (-pk * sc[k][d]);
-            if (useU) v += Ak * (-zc[k][d]);
-            F[k][d] = v + rho[k] * P.accel[k][d];
+            const FF<T> v = ff_mul(acc[k][d], m12);
+            F[k][d] = fma(rho[k], P.accel[k][d], v.hi + v.lo);
         }
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -280,7 +426,7 @@ __device__ __forceinline__ void interaction_force(const KArgs<T>& a, const Node&
 // f^eq(rho, u+du) - f^eq(rho, u) for direction i, expanded so that small du
 // does not cancel: w rho [3 e.du + 4.5 (e.(2u+du)) (e.du) - 1.5 (2u+du).du]
 template <class L, typename T>
-__device__ __forceinline__ T edm_term(int i, T rho, const T (&u)[3], const T (&du)[3])
+LBM_HD T edm_term(int i, T rho, const T (&u)[3], const T (&du)[3])
 {
     const T s0 = T(2) * u[0] + du[0], s1 = T(2) * u[1] + du[1], s2 = T(2) * u[2] + du[2];
     T edu = T(0), es = T(0);
@@ -292,7 +438,7 @@ __device__ __forceinline__ T edm_term(int i, T rho, const T (&u)[3], const T (&d
 }
 
 template <class L, typename T>
-__device__ __forceinline__ T feq(int i, T rho, const T (&u)[3], T uu)
+LBM_HD T feq(int i, T rho, const T (&u)[3], T uu)
 {
     T eu = T(0);
     if (L::ex(i)) eu += L::ex(i) > 0 ? u[0] : -u[0];
@@ -301,22 +447,43 @@ __device__ __forceinline__ T feq(int i, T rho, const T (&u)[3], T uu)
     return T(L::w(i)) * rho * (T(1) + T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu);
 }
 
+// f^eq_i = w_i rho (1 + 3 e.u + 4.5 (e.u)^2 - 1.5 u.u) split as hi + lo, with
+// hi the rounded product w_i rho (w_i itself carried as hi + lo). The
+// non-equilibrium part f_i - f^eq_i is then formed as (f_i - hi) - lo, where
+// f_i - hi is exact for f_i close to w_i rho.
+template <class L, typename T>
+LBM_HD void feq_split(int i, T rho, const T (&u)[3], T uu, T& hi, T& lo)
+{
+    T eu = T(0);
+    if (L::ex(i)) eu += L::ex(i) > 0 ? u[0] : -u[0];
+    if (L::ey(i)) eu += L::ey(i) > 0 ? u[1] : -u[1];
+    if (L::ez(i)) eu += L::ez(i) > 0 ? u[2] : -u[2];
+    const T poly = fma(eu, fma(T(4.5), eu, T(3)), T(-1.5) * uu);
+    const double w = L::w(i);
+    const T w_hi = T(w), w_lo = T(w - (double)T(w));
+    const FF<T> wr = ff_two_prod(w_hi, rho);
+    hi = wr.hi;
+    lo = fma(wr.hi, poly, fma(w_lo, rho, wr.lo));
+}
+
+// Collision and EDM forcing of one component at one node. The update is formed
+// as f_i + (edm_i - relax_i) so that only one rounding lands on f_i.
 template <class L, typename T, int COLL>
-__device__ __forceinline__ void collide(const Params<T>& P, int k, T (&f)[L::Q], T rho, const T (&u)[3],
-                                        const T (&du)[3])
+LBM_HD void collide(const Params<T>& P, int k, T (&f)[L::Q], T rho, const T (&u)[3], const T (&du)[3])
 {
     const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    T neq[L::Q];
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        T hi, lo;
+        feq_split<L, T>(i, rho, u, uu, hi, lo);
+        neq[i] = (f[i] - hi) - lo;
+    }
     if (COLL == COLL_BGK) {
         const T om = P.omega[k];
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) {
-            const T fe = feq<L, T>(i, rho, u, uu);
-            f[i] = f[i] + om * (fe - f[i]) + edm_term<L, T>(i, rho, u, du);
-        }
+        for (int i = 0; i < L::Q; ++i) f[i] = f[i] + fma(-om, neq[i], edm_term<L, T>(i, rho, u, du));
     } else {
-        T neq[L::Q];
-#pragma unroll
-        for (int i = 0; i < L::Q; ++i) neq[i] = f[i] - feq<L, T>(i, rho, u, uu);
         T m[L::Q];
 #pragma unroll
         for (int a = 0; a < L::Q; ++a) {
@@ -343,7 +510,7 @@ __device__ __forceinline__ void collide(const Params<T>& P, int k, T (&f)[L::Q],
                 else if (c == -1) acc -= m[a];
                 else if (c != 0) acc += T(c) * m[a];
             }
-            f[i] = f[i] - acc + edm_term<L, T>(i, rho, u, du);
+            f[i] = f[i] + (edm_term<L, T>(i, rho, u, du) - acc);
         }
     }
 }
@@ -353,7 +520,7 @@ __device__ __forceinline__ void collide(const Params<T>& P, int k, T (&f)[L::Q],
 // ---------------------------------------------------------------------------
 
 template <typename T>
-__device__ __forceinline__ bool bad_density(T r)
+LBM_HD bool bad_density(T r)
 {
     return !(r > T(0)) || !(r < T(1e30));
 }
@@ -370,13 +537,10 @@ __global__ void __launch_bounds__(256) k_density(const KArgs<T> a)
     for (int k = 0; k < K; ++k) {
         T f[L::Q];
         gather_k<L, T, GEOM>(a.f_src, a.p, a.solid, nd, k, f);
-        T r = T(0);
-#pragma unroll
-        for (int i = 0; i < L::Q; ++i) r += f[i];
+        const T r = density<L, T>(f);
         T ps, U;
         clamp |= pseudopotential(a.p, k, r, ps, U);
         a.psi[(long long)k * N + nd.n] = ps;
-        if (a.p.needs_U) a.U[(long long)k * N + nd.n] = U;
         if (GEOM) a.rho[(long long)k * N + nd.n] = r;
         bad |= bad_density(r);
     }
@@ -409,7 +573,6 @@ __global__ void __launch_bounds__(256) k_virtual(const KArgs<T> a)
         T ps, U;
         pseudopotential(P, k, r, ps, U);
         a.psi[(long long)k * N + s] = ps;
-        if (P.needs_U) a.U[(long long)k * N + s] = U;
         a.rho[(long long)k * N + s] = r;
     }
 }
@@ -519,7 +682,7 @@ __global__ void __launch_bounds__(256) k_get_pops(const KArgs<T> a)
 
 // rho and u = (j + F/2) / rho of one component or of the mixture at one node
 template <class L, typename T, int K, bool GEOM>
-__device__ __forceinline__ void node_macro(const KArgs<T>& a, const Node& nd, int comp, T& r_out,
+LBM_HD void node_macro(const KArgs<T>& a, const Node& nd, int comp, T& r_out,
                                            T (&u_out)[3], T (&rk)[K], T (&mk)[K][3])
 {
     T f[L::Q];

@@ -25,7 +25,6 @@ struct lbm_ctx {
     void* fbuf[2];          // population buffers, [K][Q][N]
     int cur;                // buffer holding the pre-stream populations
     void* psi;
-    void* U;
     void* rho;
     uint8_t* solid;
     int* bsolid;
@@ -137,7 +136,7 @@ double eos_alpha(int eos, double omega, double Tr)
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t f, psi, U, rho, solid, bsolid, uprev, status, partials, totals, total;
+    size_t f, psi, rho, solid, bsolid, uprev, status, partials, totals, total;
 };
 
 bool fin(double v) { return std::isfinite(v); }
@@ -190,13 +189,6 @@ lbm_status validate(const lbm_params* p)
     return LBM_OK;
 }
 
-bool needs_U(const lbm_params* p)
-{
-    for (int k = 0; k < p->ncomp; ++k)
-        if (p->A[k] != 0.0) return true;
-    return false;
-}
-
 Layout layout_of(const lbm_params* p)
 {
     const int Q = p->lattice == LBM_D2Q9 ? 9 : 19;
@@ -208,7 +200,6 @@ Layout layout_of(const lbm_params* p)
     size_t off = 0;
     L.f = off;        off += 2 * align256(K * Q * N * e);
     L.psi = off;      off += align256(K * N * e);
-    L.U = off;        off += needs_U(p) ? align256(K * N * e) : 0;
     L.rho = off;      off += align256(K * N * e);
     L.solid = off;    off += align256(N);
     L.bsolid = off;   off += align256(N * sizeof(int));
@@ -230,7 +221,6 @@ void fill_params(const lbm_ctx* c, Params<T>& P)
     P.ncomp = p->ncomp;
     P.collision = p->collision == LBM_MRT ? COLL_MRT : COLL_BGK;
     P.common_velocity = p->velocity == LBM_UEQ_COMMON;
-    P.needs_U = needs_U(p);
     for (int f = 0; f < 6; ++f) P.bc[f] = (c->D == 2 && f >= 4) ? BC_PERIODIC : p->bc[f];
     const bool d2 = p->lattice == LBM_D2Q9;
     for (int k = 0; k < 2; ++k) {
@@ -249,7 +239,19 @@ void fill_params(const lbm_ctx* c, Params<T>& P)
         P.alphaT[k] = (T)eos_alpha(p->eos[kk], p->eos_omega[kk], p->T_red[kk]);
         P.sqrtT[k] = (T)std::sqrt(c->T[kk]);
         P.alpha[k] = (T)p->alpha[kk];
+        {
+            const double b = p->eos_b[kk], RT = p->eos_R[kk] * c->T[kk];
+            const double att = p->eos[kk] == EOS_RK ? p->eos_a[kk] / std::sqrt(c->T[kk])
+                                                    : p->eos_a[kk] * eos_alpha(p->eos[kk], p->eos_omega[kk], p->T_red[kk]);
+            P.eos_b_lo[k] = (T)(b - (double)P.eos_b[k]);
+            P.RT_lo[k] = (T)(RT - (double)P.RT[k]);
+            P.att[k] = (T)att;
+            P.att_lo[k] = (T)(att - (double)P.att[k]);
+            P.alpha_lo[k] = (T)(p->alpha[kk] - (double)P.alpha[k]);
+        }
         P.A[k] = (T)p->A[kk];
+        P.oneA[k] = (T)(1.0 - p->A[kk]);
+        P.oneA_lo[k] = (T)((1.0 - p->A[kk]) - (double)P.oneA[k]);
         for (int kp = 0; kp < 2; ++kp) P.g[k][kp] = (T)p->g[kk][kp < p->ncomp ? kp : 0];
         P.wet_phi[k] = (T)p->wet_phi[kk];
         P.wet_drho[k] = (T)p->wet_drho[kk];
@@ -269,7 +271,6 @@ KArgs<T> base_args(lbm_ctx* c, const Params<T>& P)
     a.f_src = (const T*)c->fbuf[c->cur];
     a.f_dst = (T*)c->fbuf[c->cur ^ 1];
     a.psi = (T*)c->psi;
-    a.U = (T*)c->U;
     a.rho = (T*)c->rho;
     a.solid = c->solid;
     a.bsolid = c->bsolid;
@@ -413,7 +414,6 @@ lbm_status lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void
     c->fbuf[1] = c->ws + L.f + fbytes;
     c->cur = 0;
     c->psi = c->ws + L.psi;
-    c->U = needs_U(p) ? (void*)(c->ws + L.U) : nullptr;
     c->rho = c->ws + L.rho;
     c->solid = (uint8_t*)(c->ws + L.solid);
     c->bsolid = (int*)(c->ws + L.bsolid);

@@ -152,7 +152,7 @@ def droplet_3d_exp(n=256, radius=30.0, width=5.0, real="f32", shape=None):
 
 def porous_two_component(shape=(400, 400, 400), porosity=0.15, corr_length=6.0, seed=7,
                          buffer=8, real="f32", theta_phi=1.2, rho_major=1.0,
-                         rho_minor=0.03, g12=0.19, gkk=-0.009, tau_w=1.0, tau_nw=0.55,
+                         rho_minor=0.06, g12=0.1, gkk=0.0, tau_w=1.0, tau_nw=0.55,
                          drho_in=0.02):
     """D3Q19 two-component Shan-Chen (psi = rho, A = 0) in a Gaussian-random-field
     porous medium (porosity 0.15, correlation length 6) with 8-lu fluid buffers.
@@ -162,7 +162,7 @@ def porous_two_component(shape=(400, 400, 400), porosity=0.15, corr_length=6.0, 
     tau_nw = 0.55, tau_w = 1.0."""
     nx, ny, nz = shape
     solid, used_seed = grf_porous_medium(shape, porosity, corr_length, seed, buffer=buffer)
-    case = base_case("D3Q19", shape, real=real, ncomp=2, psi=["rho", "rho"],
+    case = base_case("D3Q19", shape, real=real, ncomp=2, psi=["rho", "rho"], velocity="common",
                      g=[[gkk, g12], [g12, gkk]], tau=[tau_w, tau_nw],
                      wet_phi=[theta_phi, 1.0], wet_drho=[0.0, 0.0],
                      rho_lo=[0.0, 0.0], rho_hi=[rho_major * 1.5, rho_major * 1.5],

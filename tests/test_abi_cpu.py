@@ -50,8 +50,8 @@ def test_workspace_size_layout(lib):
     c = _case()
     n = lbm.lbm_workspace_size(lbm.params_from_case(c))
     N = 16 * 12 * 10
-    # two population buffers, psi, U (A != 0), rho, mask, boundary list, u snapshot
-    assert n >= 2 * 19 * N * 4 + 3 * N * 4 + N + 4 * N + 3 * N * 4
+    # two population buffers, psi, rho, mask, boundary list, u snapshot
+    assert n >= 2 * 19 * N * 4 + 2 * N * 4 + N + 4 * N + 3 * N * 4
     n64 = lbm.lbm_workspace_size(lbm.params_from_case(dict(c, real="f64")))
     assert n64 > n
     n2 = lbm.lbm_workspace_size(lbm.params_from_case(dict(c, ncomp=2)))
