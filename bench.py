@@ -34,7 +34,12 @@ WORKLOADS = {
 def make_case(name, n=256):
     from synth import cases
     if name == "pr256":
-        case, init = cases.droplets_3d_pr(n=n)
+        if n == 256:
+            case, init = cases.droplets_3d_pr(n=n)
+        else:  # smaller cubes (profiling captures, tests): radii and width scaled with the edge
+            f = n / 256.0
+            case, init = cases.droplets_3d_pr(n=n, rmin=12.0 * f, rmax=40.0 * f,
+                                              width=max(2.0, cases.PR06_WIDTH * f))
     elif name == "exp256":
         case, init = cases.droplet_3d_exp(n=n, radius=30.0 * n / 256)
     else:
@@ -42,14 +47,17 @@ def make_case(name, n=256):
     return case, init
 
 
-def algorithmic_bytes(case):
-    """Bytes each kernel must move per lattice update (DRAM, each value once):
-    collide: read K*Q populations + K psi [+ 1 B mask], write K*Q populations;
-    density: read K*Q populations [+ 1 B mask], write K psi [+ K rho next to solids]."""
+def algorithmic_bytes(case, fused=False):
+    """Bytes each kernel must move per lattice update (DRAM, each value once).
+    Two-pass schedule -- collide: read K*Q populations + K psi [+ 1 B mask], write
+    K*Q populations; density: read K*Q populations [+ 1 B mask], write K psi [+ K rho
+    next to solids]. Single-pass schedule (k_fused): read and write K*Q populations."""
     Q = 19 if case["lattice"] == "D3Q19" else 9
     e = 8 if case.get("real") == "f64" else 4
     K = int(case.get("ncomp", 1))
     geom = any(b != "periodic" for b in case.get("bc", ["periodic"] * 6))
+    if fused:
+        return {"collide": 2 * K * Q * e, "density": 0, "step": 2 * K * Q * e}
     collide = 2 * K * Q * e + K * e + (1 if geom else 0)
     density = K * Q * e + K * e + (K * e + 1 if geom else 0)
     return {"collide": collide, "density": density, "step": collide + density}
@@ -202,6 +210,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     case, init = make_case(args.workload, args.n)
+    case["schedule"] = args.schedule
     nx, ny, nz = case["shape"]
     K = int(case.get("ncomp", 1))
     N = nx * ny * nz
@@ -238,12 +247,13 @@ def run_ours(args):
 
     # --- per-kernel device time (events between the kernels of every step)
     ms, cnt = lat.profile_step(args.steps)
-    abytes = algorithmic_bytes(case)
+    fused = cnt[0] == 0
+    abytes = algorithmic_bytes(case, fused)
     t_col = ms[2] / max(cnt[2], 1) / 1e3
     t_den = ms[0] / max(cnt[0], 1) / 1e3
     peak, peak_kind = load_peaks()
     ach_col = abytes["collide"] * N / t_col / 1e9
-    ach_den = abytes["density"] * N / t_den / 1e9
+    ach_den = abytes["density"] * N / t_den / 1e9 if not fused else 0.0
     step_gbs = abytes["step"] * N * args.steps / secs / 1e9
 
     # --- end to end through the C ABI with pinned host buffers
@@ -285,10 +295,11 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload] if args.n == 256 else
                    WORKLOADS[args.workload].replace("256^3", "%d^3" % args.n), "shape": [nx, ny, nz], "components": K,
+                   "schedule": "single-pass" if fused else "two-pass",
                    "parallelism": "replicas" if world > 1 else "single-gpu",
                    "l2": "inputs larger than L2 (two %.2f GB population buffers)" % (
                        K * 19 * N * 4 / 1e9)},
-        "roofline": {"bound": "hbm", "kernel": "k_collide", "achieved": round(ach_col, 1),
+        "roofline": {"bound": "hbm", "kernel": "k_fused" if fused else "k_collide", "achieved": round(ach_col, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(ach_col / peak, 4),
                      "peak_kind": peak_kind, "traffic": None,
                      "bytes_per_lu": abytes["collide"], "ms_per_launch": round(t_col * 1e3, 4),
@@ -315,6 +326,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="pr256", choices=sorted(WORKLOADS))
+    ap.add_argument("--schedule", default="auto", choices=["auto", "two_pass"])
     ap.add_argument("--n", type=int, default=256, help="cube edge (256 = the benchmark workload; "
                     "smaller edges are for profiling captures)")
     ap.add_argument("--e2e-steps", type=int, default=200)

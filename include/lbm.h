@@ -63,6 +63,11 @@ enum { LBM_EOS_CS = 0, LBM_EOS_PR = 1, LBM_EOS_VDW = 2, LBM_EOS_RK = 3, LBM_EOS_
  * (x faces only) */
 enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL = 1, LBM_BC_PRESSURE = 2 };
 enum { LBM_HOST = 0, LBM_DEVICE = 1 };
+/* kernel schedule of a step: AUTO = single pass (psi recomputed on chip, one read and
+ * one write of the populations) on periodic D3Q19 lattices without solids, two passes
+ * (density pass + collide pass) otherwise; TWO_PASS = always two passes. Both give the
+ * same values bit for bit. */
+enum { LBM_SCHEDULE_AUTO = 0, LBM_SCHEDULE_TWO_PASS = 1 };
 
 /*
  * Problem parameters (all per component k = 0, 1; entries of absent components are ignored).
@@ -111,6 +116,7 @@ typedef struct lbm_params {
     double body_accel[2][3];
     int bc[6];
     double bc_rho[6][2];
+    int schedule;    /* LBM_SCHEDULE_AUTO | LBM_SCHEDULE_TWO_PASS */
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -170,7 +176,8 @@ lbm_status lbm_sync(lbm_ctx* ctx);
  * stream between the kernels of every step, then synchronise. ms[0], ms[1], ms[2]
  * receive the summed device time (milliseconds) of the density, virtual-density and
  * collide kernels; launches[0..2] the number of launches of each. Timing aid for the
- * benchmark; the arithmetic is that of lbm_step. */
+ * benchmark; the arithmetic is that of lbm_step. With the single-pass schedule the
+ * density slot stays 0 and the collide slot holds the single-pass kernel. */
 lbm_status lbm_profile_step(lbm_ctx* ctx, int nsteps, double* ms, long long* launches);
 
 /* Number of kernels this context has launched since creation. */

@@ -619,6 +619,8 @@ void orc_set_geometry(orc_sim* s, const uint8_t* solid)
     }
 }
 
+static void pressure_faces_on(orc_sim* s, double* farr, int k0, int k1);
+
 /* f^eq_i(rho, u) = w_i rho (1 + e.u/c_s^2 + (e.u)^2/(2 c_s^4) - u.u/(2 c_s^2)) */
 static double feq(const orc_sim* s, int i, double rho, const double* u)
 {
@@ -627,7 +629,8 @@ static double feq(const orc_sim* s, int i, double rho, const double* u)
     return s->w[i] * rho * (1.0 + eu / CS2 + eu * eu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2));
 }
 
-/* Post-stream populations := f^eq(rho, u) at fluid nodes (u may be NULL = rest).
+/* Post-stream populations := f^eq(rho, u) at fluid nodes (u may be NULL = rest),
+ * then the constant-density face closure, like every post-stream state.
  * u is laid out [dim][N]. */
 void orc_init_fields(orc_sim* s, int k, const double* rho, const double* u)
 {
@@ -641,10 +644,12 @@ void orc_init_fields(orc_sim* s, int k, const double* rho, const double* u)
         if (u) for (int a = 0; a < d; ++a) v[a] = u[(long)a * N + n];
         for (int i = 0; i < Q; ++i) fn[i] = feq(s, i, rho[n], v);
     }
+    pressure_faces_on(s, s->f, k, k + 1);
     s->steps = 0;
 }
 
-/* Post-stream populations given directly, [Q][N] in the oracle's velocity order. */
+/* Post-stream populations given directly, [Q][N] in the oracle's velocity order
+ * (the constant-density face closure is applied to them). */
 void orc_set_populations(orc_sim* s, int k, const double* fin)
 {
     long N = s->N;
@@ -652,6 +657,7 @@ void orc_set_populations(orc_sim* s, int k, const double* fin)
     for (long n = 0; n < N; ++n)
         for (int i = 0; i < Q; ++i)
             s->f[((long)k * N + n) * Q + i] = s->solid[n] ? 0.0 : fin[(long)i * N + n];
+    pressure_faces_on(s, s->f, k, k + 1);
 }
 void orc_get_populations(const orc_sim* s, int k, double* fout)
 {
@@ -886,9 +892,9 @@ static void stream(orc_sim* s)
  *   rho u_n = rho_b - (sum_{e.n=0} f + 2 sum_{e.n<0} f)
  *   f_i = f_opp(i) + 6 w_i rho_b u_n (e_i.n) - (1/2) e_i,t . N_t,
  *   N_t = sum_{e.n=0} f_j e_j,t  (t = components tangential to the face). */
-static void pressure_faces(orc_sim* s)
+static void pressure_faces_on(orc_sim* s, double* farr, int k0, int k1)
 {
-    int Q = s->Q, K = s->p.ncomp;
+    int Q = s->Q;
     long N = s->N;
     for (int side = 0; side < 2; ++side) {
         if (s->p.face_bc[side] != ORC_PRESSURE) continue;
@@ -898,8 +904,8 @@ static void pressure_faces(orc_sim* s)
             for (int y = 0; y < s->dims[1]; ++y) {
                 long n = node_of(s, xface, y, z);
                 if (s->solid[n]) continue;
-                for (int k = 0; k < K; ++k) {
-                    double* fn = s->fnew + ((long)k * N + n) * Q;
+                for (int k = k0; k < k1; ++k) {
+                    double* fn = farr + ((long)k * N + n) * Q;
                     double rb = s->p.face_rho[side][k];
                     double s0 = 0.0, sneg = 0.0, Nt[3] = {0, 0, 0};
                     for (int i = 0; i < Q; ++i) {
@@ -921,6 +927,8 @@ static void pressure_faces(orc_sim* s)
             }
     }
 }
+
+static void pressure_faces(orc_sim* s) { pressure_faces_on(s, s->fnew, 0, s->p.ncomp); }
 
 void orc_step(orc_sim* s, int nsteps)
 {

@@ -46,7 +46,8 @@ enum : int {
     OP_SET_POPS = 4,     // post-stream populations := given array
     OP_GET_POPS = 5,     // gather post-stream populations into an array
     OP_MACRO = 6,        // rho, u = (j + F/2) / rho into arrays
-    OP_DIAG = 7          // mass / momentum / residual partial sums (deterministic)
+    OP_DIAG = 7,         // mass / momentum / residual partial sums (deterministic)
+    OP_FUSED = 8         // single-pass step (periodic, no solids, D3Q19)
 };
 
 template <typename T>
@@ -73,6 +74,7 @@ struct KArgs {
     int want_residual;
     double* partials;    // [diag_blocks][8]
     double* totals;      // [8]
+    int zchunk;          // z planes per CTA of the single-pass step (0 = default)
     cudaStream_t stream;
 };
 

@@ -331,20 +331,25 @@ LBM_HD T density(const T (&f)[L::Q])
     return r.value();
 }
 
+// j = sum_i f_i e_i, summed over opposite pairs: (f_i - f_opp) is exact for
+// neighbouring values within a factor of two (Sterbenz), so only the few
+// pair differences are rounded when added.
 template <class L, typename T>
 LBM_HD void moments(const T (&f)[L::Q], T& rho, T (&j)[3])
 {
-    CSum<T> jx, jy, jz;
+    T jx = T(0), jy = T(0), jz = T(0);
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        if (L::ex(i)) jx.add(L::ex(i) > 0 ? f[i] : -f[i]);
-        if (L::ey(i)) jy.add(L::ey(i) > 0 ? f[i] : -f[i]);
-        if (L::ez(i)) jz.add(L::ez(i) > 0 ? f[i] : -f[i]);
+    for (int i = 1; i < L::Q; ++i) {
+        if (L::opp(i) < i) continue;
+        const T d = f[i] - f[L::opp(i)];
+        if (L::ex(i)) jx += L::ex(i) > 0 ? d : -d;
+        if (L::ey(i)) jy += L::ey(i) > 0 ? d : -d;
+        if (L::ez(i)) jz += L::ez(i) > 0 ? d : -d;
     }
     rho = density<L, T>(f);
-    j[0] = jx.value();
-    j[1] = jy.value();
-    j[2] = jz.value();
+    j[0] = jx;
+    j[1] = jy;
+    j[2] = jz;
 }
 
 // ---------------------------------------------------------------------------
@@ -362,61 +367,74 @@ LBM_HD constexpr int g_twelfths(int i)
     return (int)(36.0 * L::w(i) + 0.5);  // 12 * 3 w_i
 }
 
+// With U^k = g_kk (psi^k)^2 / 2, the pair (i, opp(i)) of Eq. software_ff_force_mcmp
+// contributes c_i e_i sum_k' g_kk' dpsi^k' w_kk' with dpsi = psi(x+e_i) - psi(x-e_i),
+// w_kk = psi^k(x) + A_k delta^k (delta = mean of the two neighbours minus psi(x)),
+// w_kk' = (1 - A_k) psi^k(x) for k' != k. Hence
+//   F^k = -(1/12) [ psi^k(x) (g_kk S^k + (1 - A_k) sum_{k'!=k} g_kk' S^k') + A_k g_kk D^k ],
+//   S^k = sum_i c_i e_i dpsi^k (accumulated as hi + lo from exact differences),
+//   D^k = sum_i c_i e_i dpsi^k delta^k (small; plain accumulation).
+// psi_at(k, ex, ey, ez) returns psi^k at x + e (e = 0: at x itself).
+template <class L, typename T, int K, class PsiAt>
+LBM_HD void interaction_force_at(const Params<T>& P, const PsiAt& psi_at, const T (&rho)[K], T (&F)[K][3])
+{
+    CSum<T> Sh[K][3];
+    T Sl[K][3], D[K][3], px[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        px[k] = psi_at(k, 0, 0, 0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Sl[k][d] = D[k][d] = T(0);
+    }
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+        if (L::opp(i) < i) continue;
+        const T c = T(g_twelfths<L>(i));
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const T p1 = psi_at(k, L::ex(i), L::ey(i), L::ez(i));
+            const T p2 = psi_at(k, -L::ex(i), -L::ey(i), -L::ez(i));
+            const FF<T> dp = ff_two_sum(p1, -p2);
+            const T dh = c * dp.hi, dl = c * dp.lo;               // c <= 4: exact
+            const T dd = dh * (T(0.5) * ((p1 - px[k]) + (p2 - px[k])));
+            if (L::ex(i)) { Sh[k][0].add(L::ex(i) > 0 ? dh : -dh); Sl[k][0] += L::ex(i) > 0 ? dl : -dl; D[k][0] += L::ex(i) > 0 ? dd : -dd; }
+            if (L::ey(i)) { Sh[k][1].add(L::ey(i) > 0 ? dh : -dh); Sl[k][1] += L::ey(i) > 0 ? dl : -dl; D[k][1] += L::ey(i) > 0 ? dd : -dd; }
+            if (L::ez(i)) { Sh[k][2].add(L::ez(i) > 0 ? dh : -dh); Sl[k][2] += L::ez(i) > 0 ? dl : -dl; D[k][2] += L::ez(i) > 0 ? dd : -dd; }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            // g_kk S^k + (1 - A_k) sum_{k' != k} g_kk' S^k' as hi + lo
+            FF<T> Sk = ff_two_sum(Sh[k][d].s, Sh[k][d].c + Sl[k][d]);
+            FF<T> tot = ff_mul(Sk, P.g[k][k]);
+#pragma unroll
+            for (int kp = 0; kp < K; ++kp) {
+                if (kp == k) continue;
+                const FF<T> Sx = ff_two_sum(Sh[kp][d].s, Sh[kp][d].c + Sl[kp][d]);
+                tot = ff_add(tot, ff_mul(ff_mul(Sx, P.g[k][kp]), FF<T>{P.oneA[k], P.oneA_lo[k]}));
+            }
+            const FF<T> v = ff_add(ff_mul(tot, px[k]), ff_of(P.A[k] * P.g[k][k] * D[k][d]));
+            const FF<T> m12 = {T(-1.0 / 12.0), T(-1.0 / 12.0 - (double)T(-1.0 / 12.0))};
+            const FF<T> Fv = ff_mul(v, m12);
+            F[k][d] = fma(rho[k], P.accel[k][d], Fv.hi + Fv.lo);
+        }
+    }
+}
+
+// psi read from the global psi array (two-pass step, macroscopic outputs)
 template <class L, typename T, int K, bool GEOM>
 LBM_HD void interaction_force(const KArgs<T>& a, const Node& nd, const T (&rho)[K], T (&F)[K][3])
 {
     const Params<T>& P = a.p;
     const long long N = P.N;
-    FF<T> acc[K][3];
-    FF<T> px[K];
-    T hA[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-#pragma unroll
-        for (int d = 0; d < 3; ++d) acc[k][d] = ff_of(T(0));
-        // (1 - A_k) psi^k(x), with 1 - A_k carried as hi + lo
-        px[k] = ff_mul(FF<T>{P.oneA[k], P.oneA_lo[k]}, a.psi[(long long)k * N + nd.n]);
-        hA[k] = T(0.5) * P.A[k];
-    }
-    // pair (i, opp(i)): c_i e_i sum_k' g_kk' (psi1 - psi2)^k' [(1-A_k) psi^k(x) + [k'=k] A_k (psi1 + psi2)^k / 2]
-#pragma unroll
-    for (int i = 1; i < L::Q; ++i) {
-        if (L::opp(i) < i) continue;
-        const int o = L::opp(i);
-        const long long m1 = stencil_nb<GEOM>(P, nd.x, nd.y, nd.z, L::ex(i), L::ey(i), L::ez(i));
-        const long long m2 = stencil_nb<GEOM>(P, nd.x, nd.y, nd.z, L::ex(o), L::ey(o), L::ez(o));
-        const T c = T(g_twelfths<L>(i));
-        T p1[K], p2[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            p1[k] = a.psi[(long long)k * N + m1];
-            p2[k] = a.psi[(long long)k * N + m2];
-        }
-        FF<T> dpsi[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) dpsi[k] = ff_two_sum(p1[k], -p2[k]);
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            FF<T> t = ff_of(T(0));
-#pragma unroll
-            for (int kp = 0; kp < K; ++kp) {
-                FF<T> w = px[k];
-                if (kp == k) w = ff_add(w, ff_mul(ff_two_sum(p1[k], p2[k]), hA[k]));
-                t = ff_add(t, ff_mul(ff_mul(dpsi[kp], w), P.g[k][kp] * c));
-            }
-            if (L::ex(i)) acc[k][0] = ff_add(acc[k][0], L::ex(i) > 0 ? t : FF<T>{-t.hi, -t.lo});
-            if (L::ey(i)) acc[k][1] = ff_add(acc[k][1], L::ey(i) > 0 ? t : FF<T>{-t.hi, -t.lo});
-            if (L::ez(i)) acc[k][2] = ff_add(acc[k][2], L::ez(i) > 0 ? t : FF<T>{-t.hi, -t.lo});
-        }
-    }
-    const FF<T> m12 = {T(-1.0 / 12.0), T(-1.0 / 12.0 - (double)T(-1.0 / 12.0))};
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const FF<T> v = ff_mul(acc[k][d], m12);
-            F[k][d] = fma(rho[k], P.accel[k][d], v.hi + v.lo);
-        }
+    const T* psi = a.psi;
+    auto at = [&](int k, int ex, int ey, int ez) -> T {
+        const long long m = (ex | ey | ez) ? stencil_nb<GEOM>(P, nd.x, nd.y, nd.z, ex, ey, ez) : nd.n;
+        return psi[(long long)k * N + m];
+    };
+    interaction_force_at<L, T, K>(P, at, rho, F);
 }
 
 // ---------------------------------------------------------------------------
@@ -619,6 +637,124 @@ __global__ void __launch_bounds__(256) k_collide(const KArgs<T> a)
         T* dst = a.f_dst + (long long)k * L::Q * N + nd.n;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) dst[(long long)i * N] = f[k][i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Single-pass step for periodic lattices without solids (D3Q19)
+// ---------------------------------------------------------------------------
+//
+// Each CTA owns a TX x TY column tile and marches through a chunk of z planes.
+// psi of planes z-1, z, z+1 lives in a three-slot shared-memory ring over the
+// tile plus a one-node halo; plane z+1 is recomputed from the pre-stream
+// populations (gather -> rho -> EOS) just before plane z is collided, so psi
+// never travels through HBM. The collide re-gathers the populations of plane z
+// (read from HBM one plane earlier, now L2/L1 resident) and writes the new
+// post-collision values. Per lattice update HBM sees one read and one write of
+// the Q populations (152 B in FP32) instead of the two-pass 236 B. The
+// arithmetic is that of the two-pass kernels, value for value.
+
+template <class L, typename T, int K>
+LBM_HD void psi_of_node(const KArgs<T>& a, int x, int y, int z, T (&out)[K])
+{
+    Node nd{x, y, z, (long long)x + (long long)a.p.nx * ((long long)y + (long long)a.p.ny * z)};
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        T f[L::Q];
+        gather_k<L, T, false>(a.f_src, a.p, nullptr, nd, k, f);
+        T U;
+        pseudopotential(a.p, k, density<L, T>(f), out[k], U);
+    }
+}
+
+template <class L, typename T, int K, int COLL, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) k_fused(const KArgs<T> a, int zchunk)
+{
+    static_assert(L::D == 3, "the z march needs a 3-D lattice");
+    constexpr int HX = TX + 2, HY = TY + 2, PL = HX * HY, NH = 2 * HX + 2 * TY;
+    __shared__ T ring[3][K][PL];
+    const Params<T>& P = a.p;
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * zchunk;
+    const int z1 = min(z0 + zchunk, nz);
+    const long long N = P.N;
+
+    // psi of one plane over tile + halo into a ring slot (coordinates wrap periodically)
+    auto plane = [&](int zp, int slot) {
+        const int zw = ((zp % nz) + nz) % nz;
+        T v[K];
+        psi_of_node<L, T, K>(a, (x0 + tx) % nx, (y0 + ty) % ny, zw, v);
+#pragma unroll
+        for (int k = 0; k < K; ++k) ring[slot][k][(ty + 1) * HX + tx + 1] = v[k];
+        for (int h = tid; h < NH; h += TX * TY) {
+            int hx, hy;
+            if (h < HX) { hx = h - 1; hy = -1; }
+            else if (h < 2 * HX) { hx = h - HX - 1; hy = TY; }
+            else if (h < 2 * HX + TY) { hx = -1; hy = h - 2 * HX; }
+            else { hx = TX; hy = h - 2 * HX - TY; }
+            const int xw = (x0 + hx + nx) % nx, yw = (y0 + hy + ny) % ny;
+            psi_of_node<L, T, K>(a, xw, yw, zw, v);
+#pragma unroll
+            for (int k = 0; k < K; ++k) ring[slot][k][(hy + 1) * HX + hx + 1] = v[k];
+        }
+    };
+
+    plane(z0 - 1, 0);
+    plane(z0, 1);
+    for (int z = z0; z < z1; ++z) {
+        const int rel = z - z0;
+        plane(z + 1, (rel + 2) % 3);
+        __syncthreads();
+        const int x = x0 + tx, y = y0 + ty;
+        if (x < nx && y < ny) {
+            Node nd{x, y, z, (long long)x + (long long)nx * ((long long)y + (long long)ny * z)};
+            T f[K][L::Q];
+            T rho[K], j[K][3];
+            bool bad = false;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                gather_k<L, T, false>(a.f_src, P, nullptr, nd, k, f[k]);
+                moments<L, T>(f[k], rho[k], j[k]);
+                bad |= bad_density(rho[k]);
+            }
+            const int sm = rel % 3, sc = (rel + 1) % 3, sp = (rel + 2) % 3;
+            auto at = [&](int k, int ex, int ey, int ez) -> T {
+                const int slot = ez < 0 ? sm : (ez > 0 ? sp : sc);
+                return ring[slot][k][(ty + 1 + ey) * HX + tx + 1 + ex];
+            };
+            T F[K][3];
+            interaction_force_at<L, T, K>(P, at, rho, F);
+            T uc[3] = {T(0), T(0), T(0)};
+            if (K > 1 && P.common_velocity) {
+                T den = T(0);
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    den += rho[k] * P.omega[k];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) uc[d] += j[k][d] * P.omega[k];
+                }
+#pragma unroll
+                for (int d = 0; d < 3; ++d) uc[d] /= den;
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                T u[3], du[3];
+                const T inv = T(1) / rho[k];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    u[d] = (K > 1 && P.common_velocity) ? uc[d] : j[k][d] * inv;
+                    du[d] = F[k][d] * inv;
+                }
+                collide<L, T, COLL>(P, k, f[k], rho[k], u, du);
+                T* dst = a.f_dst + (long long)k * L::Q * N + nd.n;
+#pragma unroll
+                for (int i = 0; i < L::Q; ++i) dst[(long long)i * N] = f[k][i];
+            }
+            if (bad) atomicAdd(a.status + ST_UNSTABLE, 1);
+        }
+        __syncthreads();
     }
 }
 
@@ -826,6 +962,17 @@ cudaError_t run_k(int op, const KArgs<T>& a)
         if (a.n_bsolid > 0) k_virtual<L, T, K><<<(a.n_bsolid + 255) / 256, 256, 0, a.stream>>>(a);
         break;
     case OP_COLLIDE: k_collide<L, T, K, COLL, GEOM><<<g, b, 0, a.stream>>>(a); break;
+    case OP_FUSED:
+        if constexpr (L::D == 3 && !GEOM) {
+            constexpr int TX = 32, TY = 8;
+            const int zc = a.zchunk > 0 ? a.zchunk : 32;
+            const dim3 fb(TX, TY, 1);
+            const dim3 fg((a.p.nx + TX - 1) / TX, (a.p.ny + TY - 1) / TY, (a.p.nz + zc - 1) / zc);
+            k_fused<L, T, K, COLL, TX, TY><<<fg, fb, 0, a.stream>>>(a, zc);
+        } else {
+            return cudaErrorInvalidValue;
+        }
+        break;
     case OP_INIT_EQ: k_unstream<L, T, GEOM, true><<<g, b, 0, a.stream>>>(a); break;
     case OP_SET_POPS: k_unstream<L, T, GEOM, false><<<g, b, 0, a.stream>>>(a); break;
     case OP_GET_POPS: k_get_pops<L, T, GEOM><<<g, b, 0, a.stream>>>(a); break;

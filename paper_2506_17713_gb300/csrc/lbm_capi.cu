@@ -186,6 +186,7 @@ lbm_status validate(const lbm_params* p)
             if (p->bc[f] == LBM_BC_PRESSURE && !(p->bc_rho[f][k] > 0)) return LBM_ERR_INVALID_ARG;
     }
     if (p->ncomp == 2 && p->g[0][1] != p->g[1][0]) return LBM_ERR_INVALID_ARG;
+    if (p->schedule != LBM_SCHEDULE_AUTO && p->schedule != LBM_SCHEDULE_TWO_PASS) return LBM_ERR_INVALID_ARG;
     return LBM_OK;
 }
 
@@ -315,9 +316,20 @@ cudaError_t fields_pass(lbm_ctx* c, const Params<T>& P)
     return e;
 }
 
+bool use_fused(const lbm_ctx* c)
+{
+    return c->prm.schedule == LBM_SCHEDULE_AUTO && c->D == 3 && !c->geom;
+}
+
 template <typename T>
 cudaError_t step_once(lbm_ctx* c, const Params<T>& P)
 {
+    if (use_fused(c)) {
+        KArgs<T> a = base_args<T>(c, P);
+        const cudaError_t e = dispatch<T>(c, OP_FUSED, a);
+        if (e == cudaSuccess) c->cur ^= 1;
+        return e;
+    }
     cudaError_t e = fields_pass<T>(c, P);
     if (e != cudaSuccess) return e;
     KArgs<T> a = base_args<T>(c, P);
@@ -711,19 +723,20 @@ lbm_status profile_t(lbm_ctx* c, int nsteps, double* ms, long long* nl, const Pa
     cudaError_t e = cudaSuccess;
     for (int s = 0; s < nsteps && e == cudaSuccess; ++s) {
         KArgs<T> a = base_args<T>(c, P);
+        const bool fused = use_fused(c);
         e = cudaEventRecord(ev[0], c->stream);
-        if (e == cudaSuccess) e = dispatch<T>(c, OP_DENSITY, a);
+        if (e == cudaSuccess && !fused) e = dispatch<T>(c, OP_DENSITY, a);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
-        if (e == cudaSuccess && c->n_bsolid > 0) e = dispatch<T>(c, OP_VIRTUAL, a);
+        if (e == cudaSuccess && !fused && c->n_bsolid > 0) e = dispatch<T>(c, OP_VIRTUAL, a);
         if (e == cudaSuccess) e = cudaEventRecord(ev[2], c->stream);
-        if (e == cudaSuccess) e = dispatch<T>(c, OP_COLLIDE, a);
+        if (e == cudaSuccess) e = dispatch<T>(c, fused ? OP_FUSED : OP_COLLIDE, a);
         if (e == cudaSuccess) e = cudaEventRecord(ev[3], c->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
         if (e != cudaSuccess) break;
         c->cur ^= 1;
         float t;
         for (int k = 0; k < 3; ++k) {
-            if (k == 1 && c->n_bsolid == 0) continue;
+            if ((k == 1 && c->n_bsolid == 0) || (k < 2 && fused)) continue;
             e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
             if (e != cudaSuccess) break;
             acc[k] += t;

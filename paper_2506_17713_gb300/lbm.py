@@ -51,6 +51,7 @@ class lbm_params(C.Structure):
         ("rho_min", C.c_double * 2), ("rho_max", C.c_double * 2),
         ("body_accel", (C.c_double * 3) * 2),
         ("bc", C.c_int * 6), ("bc_rho", (C.c_double * 2) * 6),
+        ("schedule", C.c_int),
     ]
 
 
@@ -258,6 +259,7 @@ def params_from_case(case):
     for f in range(6):
         for k in range(2):
             p.bc_rho[f][k] = float(br[f, k])
+    p.schedule = {"auto": 0, "two_pass": 1}[case.get("schedule", "auto")]
     return p
 
 

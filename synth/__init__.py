@@ -91,10 +91,12 @@ def droplet_field(shape_xyz, centers, radii, rho_l, rho_g, width, periodic=True)
     return rho_g + (rho_l - rho_g) * s
 
 
-def random_droplets(shape_xyz, count, rmin, rmax, width, seed, max_tries=100000):
+def random_droplets(shape_xyz, count, rmin, rmax, width, seed, max_tries=100000, gap_widths=3.0):
     """Centres and radii of `count` droplets with radii U[rmin, rmax], placed at
     uniformly random positions in a periodic box by rejection so that any two
-    are separated by at least r_i + r_j + w (minimum image)."""
+    are separated by at least r_i + r_j + gap_widths * w (minimum image): with
+    three interface widths between surfaces the tanh tails leave no bridge of
+    intermediate (spinodal) density between neighbours."""
     nx, ny, nz = shape_xyz
     dims = [nx, ny, nz] if nz > 1 else [nx, ny]
     u = uniform(seed, max_tries * 4)
@@ -113,7 +115,7 @@ def random_droplets(shape_xyz, count, rmin, rmax, width, seed, max_tries=100000)
                 dd = abs(c[a] - c2[a])
                 dd = min(dd, dims[a] - dd)
                 d2 += dd * dd
-            if d2 < (r + r2 + width) ** 2:
+            if d2 < (r + r2 + gap_widths * width) ** 2:
                 ok = False
                 break
         if ok:
