@@ -79,11 +79,21 @@ def compare(lat, orc, tol, comps=None):
         comps = comps + [-1]
     worst = 0.0
     atol = ATOL[lat.case.get("real", "f32")]
+    # the mixture velocity sum_k (j^k + F^k/2) / sum_k rho^k of counter-flowing
+    # components is a difference of larger terms; its error is measured on the
+    # scale of the component velocities it is made of
+    uscale = 0.0
+    if lat.K > 1:
+        uscale = max(np.abs(orc.macroscopic(k)[1]).max() for k in range(lat.K))
     for k in comps:
         rg, ug = lat.macroscopic_host(k)
         ro, uo = orc.macroscopic(k)
         assert np.isfinite(rg).all() and np.isfinite(ug).all()
-        e = [rel_linf(rg, ro)] + [rel_linf(ug[d], uo[d], atol) for d in range(lat.D)]
+        if k < 0:
+            e = [rel_linf(rg, ro)] + [max(np.abs(ug[d] - uo[d]).max() - atol, 0.0) / max(uscale, np.abs(uo[d]).max())
+                                      for d in range(lat.D)]
+        else:
+            e = [rel_linf(rg, ro)] + [rel_linf(ug[d], uo[d], atol) for d in range(lat.D)]
         worst = max(worst, max(e))
         assert max(e) <= tol, (k, e)
     return worst
