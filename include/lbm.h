@@ -192,6 +192,33 @@ void lbm_destroy(lbm_ctx* ctx);
 /* Static string naming a status. */
 const char* lbm_status_str(lbm_status s);
 
+/*
+ * Mass without allocation. The paper has no counterpart: this is a service for callers
+ * that cannot allocate device memory at all -- code running while a CUDA graph is being
+ * captured, processes where a framework owns every allocation, or callers whose memory
+ * is used up by the lattice itself. It returns the same sums as the mass part of
+ * lbm_diagnostics, from populations the caller already holds.
+ *
+ *   p     lattice parameters; lattice, nx, ny, nz, ncomp and real are used.
+ *   d_f   device pointer, post-stream populations [ncomp][Q][N] of the real type of p,
+ *         the layout lbm_get_populations writes (solid nodes hold 0).
+ *   mass  host pointer, ncomp doubles: sum over nodes of sum_i f_i, per component, summed
+ *         in FP64 in a fixed order.
+ *   stream  cudaStream_t (NULL = legacy default stream); the call synchronises it.
+ *
+ * No cudaMalloc, cudaFree or allocating library routine is called. The reduction's
+ * scratch is one file-scope device array of 16 KB, held by every GPU that loads the
+ * library until the process exits; it holds the partial sums of at most
+ * LBM_NOALLOC_MAX_NODES nodes (256^3), and larger lattices are rejected with
+ * LBM_ERR_INVALID_ARG before any device work. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current, so make that
+ * first call before any stream capture. Every call shares the array and leaves its last
+ * contents there; each call overwrites all it reads. Calls that overlap on the GPU
+ * (different streams, or different host threads) race on the array.
+ */
+#define LBM_NOALLOC_MAX_NODES (256 * 256 * 256)
+lbm_status lbm_mass_noalloc(const lbm_params* p, const void* d_f, double* mass, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,7 +29,7 @@ LBM_HOST, LBM_DEVICE = 0, 1
 EXPORTS = ["lbm_workspace_size", "lbm_create", "lbm_set_geometry", "lbm_init_fields", "lbm_step",
            "lbm_macroscopic", "lbm_diagnostics", "lbm_get_populations", "lbm_set_populations",
            "lbm_velocity_set", "lbm_sync", "lbm_kernel_launches", "lbm_temperature", "lbm_destroy",
-           "lbm_status_str", "lbm_profile_step"]
+           "lbm_status_str", "lbm_profile_step", "lbm_mass_noalloc"]
 
 
 class LbmError(RuntimeError):
@@ -83,6 +83,7 @@ def library():
     L.lbm_kernel_launches.restype = C.c_longlong
     L.lbm_temperature.argtypes = [vp, C.c_int, dp]
     L.lbm_profile_step.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_longlong)]
+    L.lbm_mass_noalloc.argtypes = [pp, vp, dp, vp]
     L.lbm_destroy.argtypes = [vp]
     L.lbm_destroy.restype = None
     L.lbm_status_str.argtypes = [C.c_int]
@@ -182,6 +183,14 @@ def lbm_profile_step(ctx, nsteps):
     n = (C.c_longlong * 3)()
     _check(library().lbm_profile_step(ctx, int(nsteps), ms, n), "lbm_profile_step")
     return list(ms), list(n)
+
+
+def lbm_mass_noalloc(params, d_f, stream):
+    """Mass per component of device populations [K][Q][N], without any allocation."""
+    mass = (C.c_double * 2)()
+    _check(library().lbm_mass_noalloc(C.byref(params), C.c_void_p(d_f), mass, C.c_void_p(stream)),
+           "lbm_mass_noalloc")
+    return np.array(mass[: params.ncomp])
 
 
 def lbm_destroy(ctx):

@@ -1,0 +1,68 @@
+"""lbm_mass_noalloc: the mass reduction for callers that cannot allocate device memory.
+
+It must give the mass that lbm_diagnostics gives for the same lattice, on two calls
+in a row (the second reuses the scratch the first left behind), and it must refuse
+lattices larger than its fixed scratch covers. This file is collected last on
+purpose.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from synth import cases, random_field, random_solids
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_17713_gb300.build import build
+    build()
+
+
+def _lattice(variant):
+    from paper_2506_17713_gb300 import Lattice
+    if variant == "pr_f32":
+        case, init = cases.droplets_3d_pr(shape=(48, 40, 36), count=1, rmin=10.0, rmax=10.0, seed=5)
+        lat = Lattice(case)
+        lat.init_fields(0, init["rho"][0])
+    else:
+        shape = (23, 19, 17)
+        case = cases.base_case("D3Q19", shape, ncomp=2, psi=["rho", "rho"], velocity="common", real="f64",
+                               g=[[0.0, 0.05], [0.05, 0.0]], wet_phi=[1.1, 1.0])
+        lat = Lattice(case)
+        lat.set_geometry(random_solids(shape, 0.1, 91))
+        lat.init_fields(0, random_field(shape, 0.4, 0.6, 92))
+        lat.init_fields(1, random_field(shape, 0.4, 0.6, 93))
+    lat.step(30)
+    return lat
+
+
+@pytest.mark.parametrize("variant", ["pr_f32", "two_comp_f64_solids"])
+def test_mass_noalloc_matches_diagnostics_twice(variant):
+    import torch
+    from paper_2506_17713_gb300 import lbm
+    lat = _lattice(variant)
+    mass_ref, _ = lat.diagnostics()
+    f = torch.stack([lat.populations(k) for k in range(lat.K)]).contiguous()
+    stream = torch.cuda.current_stream().cuda_stream
+    # lbm_diagnostics sums per-node densities that an FP32 lattice has rounded to FP32
+    # (half an ulp each), this entry point the populations themselves in FP64: the
+    # totals may differ by 2^-24 relative for FP32 lattices; FP64 agrees to rounding.
+    rtol = 6e-8 if lat.case.get("real", "f32") == "f32" else 1e-12
+    for _ in range(2):
+        m = lbm.lbm_mass_noalloc(lat.params, f.data_ptr(), stream)
+        assert np.allclose(m, mass_ref, rtol=rtol, atol=0.0), (m, mass_ref)
+    lat.close()
+
+
+def test_mass_noalloc_rejects_oversized_lattice():
+    from paper_2506_17713_gb300 import lbm
+    p = lbm.params_from_case(cases.base_case("D3Q19", (257, 256, 256)))
+    mass = (C.c_double * 2)()
+    # rejected before any device work, so a dummy pointer is never touched
+    assert lbm.library().lbm_mass_noalloc(C.byref(p), C.c_void_p(256), mass, None) == 1
