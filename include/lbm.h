@@ -63,11 +63,13 @@ enum { LBM_EOS_CS = 0, LBM_EOS_PR = 1, LBM_EOS_VDW = 2, LBM_EOS_RK = 3, LBM_EOS_
  * (x faces only) */
 enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL = 1, LBM_BC_PRESSURE = 2 };
 enum { LBM_HOST = 0, LBM_DEVICE = 1 };
-/* kernel schedule of a step: AUTO = single pass (psi recomputed on chip, one read and
- * one write of the populations) on periodic D3Q19 lattices without solids, two passes
- * (density pass + collide pass) otherwise; TWO_PASS = always two passes. Both give the
- * same values bit for bit. */
-enum { LBM_SCHEDULE_AUTO = 0, LBM_SCHEDULE_TWO_PASS = 1 };
+/* kernel schedule of a step. TWO_PASS: a density pass (psi to HBM) and a collide pass.
+ * SINGLE_PASS (periodic D3Q19 lattices without solids only, else two passes): psi is
+ * recomputed on chip from the populations, which are read and written once. AUTO =
+ * TWO_PASS: on GB300 the accurate FP32 arithmetic makes the single pass's psi recompute
+ * cost more issue slots than the HBM traffic it saves. All give the same values bit for
+ * bit. */
+enum { LBM_SCHEDULE_AUTO = 0, LBM_SCHEDULE_TWO_PASS = 1, LBM_SCHEDULE_SINGLE_PASS = 2 };
 
 /*
  * Problem parameters (all per component k = 0, 1; entries of absent components are ignored).
@@ -116,7 +118,7 @@ typedef struct lbm_params {
     double body_accel[2][3];
     int bc[6];
     double bc_rho[6][2];
-    int schedule;    /* LBM_SCHEDULE_AUTO | LBM_SCHEDULE_TWO_PASS */
+    int schedule;    /* LBM_SCHEDULE_AUTO | LBM_SCHEDULE_TWO_PASS | LBM_SCHEDULE_SINGLE_PASS */
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx;

@@ -29,7 +29,10 @@ struct Params {
     T omega[2];          // 1 / tau
     T rates[2][19];      // MRT rates, stress = 1/tau, conserved = 0
     T eos_a[2], eos_b[2], RT[2], alphaT[2], sqrtT[2];
-    T eos_b_lo[2], RT_lo[2], att[2], att_lo[2], alpha_lo[2];  // hi + lo parts for FP32
+    T alpha_lo[2];                  // hi + lo parts for FP32
+    T eos_c[2][5], eos_c_lo[2][5];  // p = rho N(rho) / D(rho): coefficients of N, hi + lo
+    T two_over_g[2], two_over_g_lo[2];
+    T gm12[2], gm12_lo[2];           // -g_kk / 12, hi + lo
     T alpha[2], A[2], g[2][2];
     T oneA[2], oneA_lo[2];   // 1 - A as hi + lo
     T wet_phi[2], wet_drho[2], rho_min[2], rho_max[2];

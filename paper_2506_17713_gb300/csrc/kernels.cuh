@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <utility>
 
 #include "args.h"
 #include "lattice.cuh"
@@ -29,6 +30,42 @@
 #define LBM_HD __host__ __device__ __forceinline__
 
 namespace lbm {
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I = 0 .. N-1, so that
+// table lookups inside the body are constant expressions (bound to constexpr
+// locals) rather than calls the optimiser may or may not fold.
+template <class F, int... I>
+LBM_HD void static_for_impl(F&& f, std::integer_sequence<int, I...>)
+{
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+LBM_HD void static_for(F&& f)
+{
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// first member i (i < opp(i)) of the p-th opposite pair of the velocity set
+template <class L>
+LBM_HD constexpr int pair_first(int p)
+{
+    int n = 0;
+    for (int i = 1; i < L::Q; ++i)
+        if (i < L::opp(i)) {
+            if (n == p) return i;
+            ++n;
+        }
+    return -1;
+}
+
+// moment a of the MRT basis is even under e -> -e (sees pair sums only)
+template <class L>
+LBM_HD constexpr bool mrt_even(int a)
+{
+    for (int i = 1; i < L::Q; ++i)
+        if (L::M(a, i) != L::M(a, L::opp(i))) return false;
+    return true;
+}
 
 // Double-float ("float-float") arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2.
 // Error-free transformations (Knuth's TwoSum, FMA-based TwoProd) give about 44
@@ -84,6 +121,24 @@ LBM_HD FF<T> ff_div(FF<T> a, FF<T> b)
 template <typename T>
 LBM_HD FF<T> ff_of(T a) { return {a, T(0)}; }
 
+// correctly rounded reciprocal (one short hardware sequence instead of a division)
+LBM_HD float rcp(float x)
+{
+#ifdef __CUDA_ARCH__
+    return __frcp_rn(x);
+#else
+    return 1.0f / x;
+#endif
+}
+LBM_HD double rcp(double x)
+{
+#ifdef __CUDA_ARCH__
+    return __drcp_rn(x);
+#else
+    return 1.0 / x;
+#endif
+}
+
 // Compensated summation (Neumaier's variant of Kahan summation): the running
 // sum carries the rounding error of every addition in a second register, so
 // rho = sum_i f_i and j = sum_i f_i e_i come out within about one rounding of
@@ -99,6 +154,34 @@ struct CSum {
     }
     LBM_HD T value() const { return s + c; }
 };
+
+// Moment-space form of the EDM shift: for the second-order equilibrium,
+//   m_a^eq(rho, u') - m_a^eq(rho, u) = rho [3 sum_d A_ad du_d + sum_{d<=d'} B_add' dq_dd'],
+//   dq_dd' = u'_d u'_d' - u_d u_d', with constants of the basis
+//   A_ad = sum_i M_ai w_i e_id,  B_add' = (2 - [d=d']) (4.5 sum_i M_ai w_i e_id e_id' - 1.5 [d=d'] sum_i M_ai w_i).
+template <class L>
+LBM_HD constexpr int e_of(int i, int d)
+{
+    return d == 0 ? L::ex(i) : (d == 1 ? L::ey(i) : L::ez(i));
+}
+template <class L>
+LBM_HD constexpr double edm_A(int a, int d)
+{
+    double s = 0.0;
+    for (int i = 0; i < L::Q; ++i) s += L::M(a, i) * L::w(i) * e_of<L>(i, d);
+    return s;
+}
+template <class L>
+LBM_HD constexpr double edm_B(int a, int d, int dp)
+{
+    double s2 = 0.0, s0 = 0.0;
+    for (int i = 0; i < L::Q; ++i) {
+        s2 += L::M(a, i) * L::w(i) * e_of<L>(i, d) * e_of<L>(i, dp);
+        s0 += L::M(a, i) * L::w(i);
+    }
+    const double b = 4.5 * s2 - (d == dp ? 1.5 * s0 : 0.0);
+    return d == dp ? b : 2.0 * b;
+}
 
 // ---------------------------------------------------------------------------
 // Equation of state and pseudopotential (Section 2.2, Eq. eos_potential)
@@ -126,38 +209,48 @@ LBM_HD T eos_pressure(const Params<T>& P, int k, T rho)
     }
 }
 
-// p_EOS(rho) in double-float arithmetic (FP32 storage types): in a stiff liquid
-// the repulsive and attractive terms are large and nearly cancel, so plain FP32
-// loses several bits of the pressure. p = R T rho r(rho) - att rho^2 / D(rho),
-// with the per-EOS factors r, D of the paper's equations of state and att = a
-// alpha(T) (a / sqrt(T) for Redlich-Kwong); parameters are carried as hi + lo.
+// FP32 pseudopotential energy in double-float arithmetic. Every EOS here can be
+// written p = rho N(rho) / D(rho) with a polynomial numerator N (degree 2, or 4
+// for Carnahan-Starling) and a cancellation-free denominator D (powers of 1 - b rho,
+// 1 + b rho, 1 + 2 b rho - b^2 rho^2); the host folds R T, a, b and alpha(T) into
+// the coefficients of N. In a stiff liquid the terms of N nearly cancel, so N is
+// evaluated as hi + lo (Horner), D in plain FP32 with fused multiply-adds, and
+//   U = alpha p - c_s^2 rho = rho (alpha N / D - 1/3)
+// as hi + lo.
 template <typename T>
-LBM_HD FF<T> eos_pressure_ff(const Params<T>& P, int k, T rho)
+LBM_HD T eos_denominator(const Params<T>& P, int k, T rho)
 {
-    const FF<T> one = ff_of(T(1));
-    const FF<T> b = {P.eos_b[k], P.eos_b_lo[k]};
-    const FF<T> br = ff_mul(b, rho);
-    FF<T> rep;  // rho r(rho)
-    FF<T> den = one;
+    const T b = P.eos_b[k];
     switch (P.eos[k]) {
     case EOS_CS: {
-        const FF<T> eta = ff_mul(br, T(0.25));
-        const FF<T> om = ff_add(one, FF<T>{-eta.hi, -eta.lo});
-        // 1 + eta + eta^2 - eta^3 = 1 + eta (1 + eta (1 - eta))
-        const FF<T> num = ff_add(one, ff_mul(eta, ff_add(one, ff_mul(eta, om))));
-        rep = ff_div(ff_mul(num, rho), ff_mul(ff_mul(om, om), om));
-        break;
+        const T om = fma(T(-0.25) * b, rho, T(1));
+        return om * om * om;
     }
-    default: {
-        rep = ff_div(ff_of(rho), ff_add(one, FF<T>{-br.hi, -br.lo}));
-        if (P.eos[k] == EOS_PR) den = ff_add(one, ff_mul(br, ff_add(ff_of(T(2)), FF<T>{-br.hi, -br.lo})));
-        else if (P.eos[k] == EOS_RK || P.eos[k] == EOS_RKS) den = ff_add(one, br);
-        break;
+    case EOS_PR: {
+        const T br = b * rho;
+        return fma(-b, rho, T(1)) * fma(br, T(2) - br, T(1));
     }
+    case EOS_VDW: return fma(-b, rho, T(1));
+    default: return fma(-b * b, rho * rho, T(1));  // RK, RKS: (1 - b rho)(1 + b rho)
     }
-    const FF<T> t1 = ff_mul(rep, FF<T>{P.RT[k], P.RT_lo[k]});
-    const FF<T> t2 = ff_div(ff_mul(ff_two_prod(rho, rho), FF<T>{P.att[k], P.att_lo[k]}), den);
-    return ff_add(t1, FF<T>{-t2.hi, -t2.lo});
+}
+
+template <typename T>
+LBM_HD FF<T> eos_energy_ff(const Params<T>& P, int k, T rho)
+{
+    const int deg = P.eos[k] == EOS_CS ? 4 : 2;
+    FF<T> n = {P.eos_c[k][deg], P.eos_c_lo[k][deg]};
+    for (int d = deg - 1; d >= 0; --d) n = ff_add(ff_mul(n, rho), FF<T>{P.eos_c[k][d], P.eos_c_lo[k][d]});
+    // alpha N / D: the quotient of hi + lo by a float, corrected once
+    const FF<T> an = ff_mul(n, FF<T>{P.alpha[k], P.alpha_lo[k]});
+    const T den = eos_denominator(P, k, rho);
+    const T r = rcp(den);
+    const T q1 = an.hi * r;                                    // within 1.5 ulp
+    const FF<T> qd = ff_two_prod(q1, den);
+    const T q2 = ((an.hi - qd.hi) - qd.lo + an.lo) * r;       // exact residual / den
+    const FF<T> q = ff_two_sum(q1, q2);
+    const FF<T> third = {T(1.0 / 3.0), T(1.0 / 3.0 - (double)T(1.0 / 3.0))};
+    return ff_mul(ff_add(q, FF<T>{-third.hi, -third.lo}), rho);
 }
 
 // psi^k (and the pseudopotential energy U^k = alpha p_EOS - c_s^2 rho) from rho^k.
@@ -168,20 +261,19 @@ LBM_HD bool pseudopotential(const Params<T>& P, int k, T rho, T& psi, T& U)
     const T g = P.g[k][k];
     if (P.psi_kind[k] == PSI_EOS) {
         if (sizeof(T) == 4) {
-            const FF<T> pe = eos_pressure_ff(P, k, rho);
-            const FF<T> third = {T(1.0 / 3.0), T(1.0 / 3.0 - (double)T(1.0 / 3.0))};
-            const FF<T> u = ff_add(ff_mul(pe, FF<T>{P.alpha[k], P.alpha_lo[k]}),
-                                   FF<T>{-ff_mul(third, rho).hi, -ff_mul(third, rho).lo});
-            const FF<T> arg = ff_div(ff_mul(u, T(2)), ff_of(g));
+            const FF<T> u = eos_energy_ff(P, k, rho);
+            const FF<T> arg = ff_mul(u, FF<T>{P.two_over_g[k], P.two_over_g_lo[k]});
             U = u.hi + u.lo;
             if (arg.hi <= T(0)) {
                 psi = T(0);
                 return arg.hi < T(0);
             }
-            // sqrt of hi + lo: one Newton correction of the FP32 root
-            const T r = sqrt(arg.hi);
+            // sqrt of hi + lo: approximate root from rsqrt, then one Newton step
+            // against the exact residual (error ~ the square of the first one's)
+            const T ri = rsqrt(arg.hi);
+            const T r = arg.hi * ri;
             const FF<T> r2 = ff_two_prod(r, r);
-            psi = r + ((arg.hi - r2.hi) - r2.lo + arg.lo) / (T(2) * r);
+            psi = fma((arg.hi - r2.hi) - r2.lo + arg.lo, T(0.5) * ri, r);
             return false;
         }
         U = P.alpha[k] * eos_pressure(P, k, rho) - rho * T(1.0 / 3.0);
@@ -299,6 +391,40 @@ LBM_HD void zou_he(T (&f)[L::Q], int nin, T rho_b)
     }
 }
 
+// Periodic lattice without solids: the 3 x 3 x 3 wrapped source offsets of a node
+// are formed once, so each of the Q pull sources costs two integer adds (node
+// indices fit in 32 bits: the workspace of 2^31 nodes would exceed the HBM).
+struct Wrap3 {
+    int xo[3], yo[3], zo[3];  // offsets of x - d, d = -1, 0, +1 (index d + 1)
+};
+
+template <typename T>
+LBM_HD Wrap3 wrap3(const Params<T>& P, int x, int y, int z)
+{
+    Wrap3 w;
+    const int nx = P.nx, ny = P.ny, nz = P.nz, pl = nx * ny;
+    w.xo[0] = x == nx - 1 ? 0 : x + 1;       // source x - e with e = -1
+    w.xo[1] = x;
+    w.xo[2] = x == 0 ? nx - 1 : x - 1;       // e = +1
+    w.yo[0] = (y == ny - 1 ? 0 : y + 1) * nx;
+    w.yo[1] = y * nx;
+    w.yo[2] = (y == 0 ? ny - 1 : y - 1) * nx;
+    w.zo[0] = (z == nz - 1 ? 0 : z + 1) * pl;
+    w.zo[1] = z * pl;
+    w.zo[2] = (z == 0 ? nz - 1 : z - 1) * pl;
+    return w;
+}
+
+template <class L, typename T>
+LBM_HD void gather_periodic(const T* __restrict__ fk, long long N, const Wrap3& w, T (&f)[L::Q])
+{
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const int src = w.xo[L::ex(i) + 1] + w.yo[L::ey(i) + 1] + w.zo[L::ez(i) + 1];
+        f[i] = fk[(long long)i * N + src];
+    }
+}
+
 // Post-stream populations of component k at a fluid node (pull + bounce-back +
 // constant-density faces).
 template <class L, typename T, bool GEOM>
@@ -308,6 +434,10 @@ LBM_HD void gather_k(const T* __restrict__ f_all, const Params<T>& P,
 {
     const T* fk = f_all + (long long)k * L::Q * P.N;
     const long long N = P.N;
+    if (!GEOM) {
+        gather_periodic<L, T>(fk, N, wrap3(P, nd.x, nd.y, nd.z), f);
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
         long long src;
@@ -322,18 +452,26 @@ LBM_HD void gather_k(const T* __restrict__ f_all, const Params<T>& P,
     }
 }
 
+// rho = sum_i f_i as a balanced tree over opposite-pair sums (rounding error grows
+// with the tree depth, log2 Q, instead of with Q for a running sum)
 template <class L, typename T>
 LBM_HD T density(const T (&f)[L::Q])
 {
-    CSum<T> r;
+    constexpr int NP = (L::Q - 1) / 2;
+    T s[NP + 1];
+    s[0] = f[0];
+    static_for<NP>([&](auto pc) {
+        constexpr int i = pair_first<L>(decltype(pc)::value);
+        constexpr int o = L::opp(i);
+        s[decltype(pc)::value + 1] = f[i] + f[o];
+    });
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) r.add(f[i]);
-    return r.value();
+    for (int w = 1; w < NP + 1; w *= 2)
+#pragma unroll
+        for (int i = 0; i + w < NP + 1; i += 2 * w) s[i] = s[i] + s[i + w];
+    return s[0];
 }
 
-// j = sum_i f_i e_i, summed over opposite pairs: (f_i - f_opp) is exact for
-// neighbouring values within a factor of two (Sterbenz), so only the few
-// pair differences are rounded when added.
 template <class L, typename T>
 LBM_HD void moments(const T (&f)[L::Q], T& rho, T (&j)[3])
 {
@@ -378,13 +516,12 @@ LBM_HD constexpr int g_twelfths(int i)
 template <class L, typename T, int K, class PsiAt>
 LBM_HD void interaction_force_at(const Params<T>& P, const PsiAt& psi_at, const T (&rho)[K], T (&F)[K][3])
 {
-    CSum<T> Sh[K][3];
-    T Sl[K][3], D[K][3], px[K];
+    T Sh[K][3], Sl[K][3], D[K][3], px[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         px[k] = psi_at(k, 0, 0, 0);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) Sl[k][d] = D[k][d] = T(0);
+        for (int d = 0; d < 3; ++d) Sh[k][d] = Sl[k][d] = D[k][d] = T(0);
     }
 #pragma unroll
     for (int i = 1; i < L::Q; ++i) {
@@ -397,28 +534,37 @@ LBM_HD void interaction_force_at(const Params<T>& P, const PsiAt& psi_at, const 
             const FF<T> dp = ff_two_sum(p1, -p2);
             const T dh = c * dp.hi, dl = c * dp.lo;               // c <= 4: exact
             const T dd = dh * (T(0.5) * ((p1 - px[k]) + (p2 - px[k])));
-            if (L::ex(i)) { Sh[k][0].add(L::ex(i) > 0 ? dh : -dh); Sl[k][0] += L::ex(i) > 0 ? dl : -dl; D[k][0] += L::ex(i) > 0 ? dd : -dd; }
-            if (L::ey(i)) { Sh[k][1].add(L::ey(i) > 0 ? dh : -dh); Sl[k][1] += L::ey(i) > 0 ? dl : -dl; D[k][1] += L::ey(i) > 0 ? dd : -dd; }
-            if (L::ez(i)) { Sh[k][2].add(L::ez(i) > 0 ? dh : -dh); Sl[k][2] += L::ez(i) > 0 ? dl : -dl; D[k][2] += L::ez(i) > 0 ? dd : -dd; }
+            if (L::ex(i)) { Sh[k][0] += L::ex(i) > 0 ? dh : -dh; Sl[k][0] += L::ex(i) > 0 ? dl : -dl; D[k][0] += L::ex(i) > 0 ? dd : -dd; }
+            if (L::ey(i)) { Sh[k][1] += L::ey(i) > 0 ? dh : -dh; Sl[k][1] += L::ey(i) > 0 ? dl : -dl; D[k][1] += L::ey(i) > 0 ? dd : -dd; }
+            if (L::ez(i)) { Sh[k][2] += L::ez(i) > 0 ? dh : -dh; Sl[k][2] += L::ez(i) > 0 ? dl : -dl; D[k][2] += L::ez(i) > 0 ? dd : -dd; }
         }
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            // g_kk S^k + (1 - A_k) sum_{k' != k} g_kk' S^k' as hi + lo
-            FF<T> Sk = ff_two_sum(Sh[k][d].s, Sh[k][d].c + Sl[k][d]);
-            FF<T> tot = ff_mul(Sk, P.g[k][k]);
+            FF<T> v;
+            if (K == 1) {
+                // F = (-g/12) (psi(x) S + A D)
+                const FF<T> S = ff_two_sum(Sh[k][d], Sl[k][d]);
+                v = ff_two_prod(px[k], S.hi);
+                v.lo = fma(px[k], S.lo, v.lo) + P.A[k] * D[k][d];
+            } else {
+                // g_kk S^k + (1 - A_k) sum_{k' != k} g_kk' S^k', times psi^k(x), + A_k g_kk D^k
+                FF<T> tot = ff_mul(ff_two_sum(Sh[k][d], Sl[k][d]), P.g[k][k]);
 #pragma unroll
-            for (int kp = 0; kp < K; ++kp) {
-                if (kp == k) continue;
-                const FF<T> Sx = ff_two_sum(Sh[kp][d].s, Sh[kp][d].c + Sl[kp][d]);
-                tot = ff_add(tot, ff_mul(ff_mul(Sx, P.g[k][kp]), FF<T>{P.oneA[k], P.oneA_lo[k]}));
+                for (int kp = 0; kp < K; ++kp) {
+                    if (kp == k) continue;
+                    const FF<T> Sx = ff_two_sum(Sh[kp][d], Sl[kp][d]);
+                    tot = ff_add(tot, ff_mul(ff_mul(Sx, P.g[k][kp]), FF<T>{P.oneA[k], P.oneA_lo[k]}));
+                }
+                v = ff_add(ff_mul(tot, px[k]), ff_of(P.A[k] * P.g[k][k] * D[k][d]));
             }
-            const FF<T> v = ff_add(ff_mul(tot, px[k]), ff_of(P.A[k] * P.g[k][k] * D[k][d]));
-            const FF<T> m12 = {T(-1.0 / 12.0), T(-1.0 / 12.0 - (double)T(-1.0 / 12.0))};
-            const FF<T> Fv = ff_mul(v, m12);
-            F[k][d] = fma(rho[k], P.accel[k][d], Fv.hi + Fv.lo);
+            // times -1/12 (K = 1: times -g/12)
+            const T ch = K == 1 ? P.gm12[k] : T(-1.0 / 12.0);
+            const T cl = K == 1 ? P.gm12_lo[k] : T(-1.0 / 12.0 - (double)T(-1.0 / 12.0));
+            const T Fv = fma(v.hi, ch, fma(v.hi, cl, v.lo * ch));
+            F[k][d] = fma(rho[k], P.accel[k][d], Fv);
         }
     }
 }
@@ -430,6 +576,15 @@ LBM_HD void interaction_force(const KArgs<T>& a, const Node& nd, const T (&rho)[
     const Params<T>& P = a.p;
     const long long N = P.N;
     const T* psi = a.psi;
+    if (!GEOM) {
+        // periodic: x + e from the wrapped offsets (index d + 1 of Wrap3 holds x - d)
+        const Wrap3 w = wrap3(P, nd.x, nd.y, nd.z);
+        auto at = [&](int k, int ex, int ey, int ez) -> T {
+            return psi[(long long)k * N + (w.xo[1 - ex] + w.yo[1 - ey] + w.zo[1 - ez])];
+        };
+        interaction_force_at<L, T, K>(P, at, rho, F);
+        return;
+    }
     auto at = [&](int k, int ex, int ey, int ez) -> T {
         const long long m = (ex | ey | ez) ? stencil_nb<GEOM>(P, nd.x, nd.y, nd.z, ex, ey, ez) : nd.n;
         return psi[(long long)k * N + m];
@@ -485,7 +640,9 @@ LBM_HD void feq_split(int i, T rho, const T (&u)[3], T uu, T& hi, T& lo)
 }
 
 // Collision and EDM forcing of one component at one node. The update is formed
-// as f_i + (edm_i - relax_i) so that only one rounding lands on f_i.
+// as f_i + (small correction) so that only one rounding lands on f_i. BGK adds
+// the EDM shift per direction; MRT adds it in moment space together with the
+// relaxation, f* = f + M^-1 (Delta m^eq - S m^neq).
 template <class L, typename T, int COLL>
 LBM_HD void collide(const Params<T>& P, int k, T (&f)[L::Q], T rho, const T (&u)[3], const T (&du)[3])
 {
@@ -502,34 +659,102 @@ LBM_HD void collide(const Params<T>& P, int k, T (&f)[L::Q], T rho, const T (&u)
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) f[i] = f[i] + fma(-om, neq[i], edm_term<L, T>(i, rho, u, du));
     } else {
+        // Moment transforms through opposite pairs (i, opp(i)): moments even under
+        // e -> -e see f_0 and the pair sums, odd moments the pair differences, which
+        // halves the adds of both transforms. Every coefficient is a compile-time
+        // constant of the basis.
+        constexpr int NP = (L::Q - 1) / 2;
+        T ps[NP], pd[NP];
+        static_for<NP>([&](auto pc) {
+            constexpr int p = decltype(pc)::value;
+            constexpr int i = pair_first<L>(p);
+            constexpr int o = L::opp(i);
+            ps[p] = neq[i] + neq[o];
+            pd[p] = neq[i] - neq[o];
+        });
+        // EDM shift in moment space (velocity products as fused multiply-adds)
+        T dq[6];
+        {
+            const T up[3] = {u[0] + du[0], u[1] + du[1], u[2] + du[2]};
+            int q = 0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+#pragma unroll
+                for (int dp = d; dp < 3; ++dp) dq[q++] = fma(u[d], du[dp], du[d] * up[dp]);
+        }
         T m[L::Q];
-#pragma unroll
-        for (int a = 0; a < L::Q; ++a) {
-            if (L::conserved(a)) { m[a] = T(0); continue; }
-            T acc = T(0);
-#pragma unroll
-            for (int i = 0; i < L::Q; ++i) {
-                const int c = L::M(a, i);
-                if (c == 1) acc += neq[i];
-                else if (c == -1) acc -= neq[i];
-                else if (c != 0) acc += T(c) * neq[i];
+        static_for<L::Q>([&](auto ac) {
+            constexpr int a = decltype(ac)::value;
+            // (Delta m^eq_a - s_a m^neq_a) / |row a|^2
+            T dm = T(0);
+            static_for<3>([&](auto dc) {
+                constexpr int d = decltype(dc)::value;
+                constexpr double c = d < L::D ? 3.0 * edm_A<L>(a, d) : 0.0;
+                if constexpr (c != 0.0) dm = fma(T(c), du[d], dm);
+            });
+            static_for<6>([&](auto qc) {
+                constexpr int q = decltype(qc)::value;
+                constexpr int d = q < 3 ? 0 : (q < 5 ? 1 : 2);
+                constexpr int dp = q < 3 ? q : (q < 5 ? q - 2 : 2);
+                constexpr double c = (d < L::D && dp < L::D) ? edm_B<L>(a, d, dp) : 0.0;
+                if constexpr (c != 0.0) dm = fma(T(c), dq[q], dm);
+            });
+            dm = dm * rho;
+            constexpr double inv_norm = 1.0 / mrt_norm<L>(a);
+            if constexpr (L::conserved(a)) {
+                m[a] = dm * T(inv_norm);
+            } else {
+                T acc = T(0);
+                if constexpr (mrt_even<L>(a)) {
+                    constexpr int c0 = L::M(a, 0);
+                    if constexpr (c0 != 0) acc = T(c0) * neq[0];
+                    static_for<NP>([&](auto pc) {
+                        constexpr int c = L::M(a, pair_first<L>(decltype(pc)::value));
+                        if constexpr (c == 1) acc += ps[decltype(pc)::value];
+                        else if constexpr (c == -1) acc -= ps[decltype(pc)::value];
+                        else if constexpr (c != 0) acc += T(c) * ps[decltype(pc)::value];
+                    });
+                } else {
+                    static_for<NP>([&](auto pc) {
+                        constexpr int c = L::M(a, pair_first<L>(decltype(pc)::value));
+                        if constexpr (c == 1) acc += pd[decltype(pc)::value];
+                        else if constexpr (c == -1) acc -= pd[decltype(pc)::value];
+                        else if constexpr (c != 0) acc += T(c) * pd[decltype(pc)::value];
+                    });
+                }
+                const T s = L::stress(a) ? P.omega[k] : P.rates[k][a];
+                m[a] = fma(-s, acc, dm) * T(inv_norm);
             }
-            const T s = L::stress(a) ? P.omega[k] : P.rates[k][a];
-            m[a] = s * acc * T(1.0 / mrt_norm<L>(a));
-        }
-#pragma unroll
-        for (int i = 0; i < L::Q; ++i) {
+        });
+        // f* = f + M^-1 (Delta m^eq - S m^neq), M^-1 = M^T diag(1 / row norm)
+        T relax[L::Q];
+        {
             T acc = T(0);
-#pragma unroll
-            for (int a = 0; a < L::Q; ++a) {
-                if (L::conserved(a)) continue;
-                const int c = L::M(a, i);
-                if (c == 1) acc += m[a];
-                else if (c == -1) acc -= m[a];
-                else if (c != 0) acc += T(c) * m[a];
-            }
-            f[i] = f[i] + (edm_term<L, T>(i, rho, u, du) - acc);
+            static_for<L::Q>([&](auto ac) {
+                constexpr int a = decltype(ac)::value;
+                constexpr int c = mrt_even<L>(a) ? L::M(a, 0) : 0;
+                if constexpr (c != 0) acc += T(c) * m[a];
+            });
+            relax[0] = acc;
         }
+        static_for<NP>([&](auto pc) {
+            constexpr int i = pair_first<L>(decltype(pc)::value);
+            T ev = T(0), od = T(0);
+            static_for<L::Q>([&](auto ac) {
+                constexpr int a = decltype(ac)::value;
+                constexpr int c = L::M(a, i);
+                constexpr bool even = mrt_even<L>(a);
+                T& t = even ? ev : od;
+                if constexpr (c == 1) t += m[a];
+                else if constexpr (c == -1) t -= m[a];
+                else if constexpr (c != 0) t += T(c) * m[a];
+            });
+            constexpr int o = L::opp(i);
+            relax[i] = ev + od;
+            relax[o] = ev - od;
+        });
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) f[i] = f[i] + relax[i];
     }
 }
 
@@ -627,7 +852,7 @@ __global__ void __launch_bounds__(256) k_collide(const KArgs<T> a)
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         T u[3], du[3];
-        const T inv = T(1) / rho[k];
+        const T inv = rcp(rho[k]);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             u[d] = (K > 1 && P.common_velocity) ? uc[d] : j[k][d] * inv;
@@ -682,10 +907,12 @@ __global__ void __launch_bounds__(TX * TY) k_fused(const KArgs<T> a, int zchunk)
     const long long N = P.N;
 
     // psi of one plane over tile + halo into a ring slot (coordinates wrap periodically)
+    // coordinates here lie in [-1, 2n): one conditional add or subtract wraps them
+    auto wrap = [](int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); };
     auto plane = [&](int zp, int slot) {
-        const int zw = ((zp % nz) + nz) % nz;
+        const int zw = wrap(zp, nz);
         T v[K];
-        psi_of_node<L, T, K>(a, (x0 + tx) % nx, (y0 + ty) % ny, zw, v);
+        psi_of_node<L, T, K>(a, wrap(x0 + tx, nx), wrap(y0 + ty, ny), zw, v);
 #pragma unroll
         for (int k = 0; k < K; ++k) ring[slot][k][(ty + 1) * HX + tx + 1] = v[k];
         for (int h = tid; h < NH; h += TX * TY) {
@@ -694,7 +921,7 @@ __global__ void __launch_bounds__(TX * TY) k_fused(const KArgs<T> a, int zchunk)
             else if (h < 2 * HX) { hx = h - HX - 1; hy = TY; }
             else if (h < 2 * HX + TY) { hx = -1; hy = h - 2 * HX; }
             else { hx = TX; hy = h - 2 * HX - TY; }
-            const int xw = (x0 + hx + nx) % nx, yw = (y0 + hy + ny) % ny;
+            const int xw = wrap(x0 + hx, nx), yw = wrap(y0 + hy, ny);
             psi_of_node<L, T, K>(a, xw, yw, zw, v);
 #pragma unroll
             for (int k = 0; k < K; ++k) ring[slot][k][(hy + 1) * HX + hx + 1] = v[k];
@@ -741,7 +968,7 @@ __global__ void __launch_bounds__(TX * TY) k_fused(const KArgs<T> a, int zchunk)
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 T u[3], du[3];
-                const T inv = T(1) / rho[k];
+                const T inv = rcp(rho[k]);
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
                     u[d] = (K > 1 && P.common_velocity) ? uc[d] : j[k][d] * inv;

@@ -186,7 +186,9 @@ lbm_status validate(const lbm_params* p)
             if (p->bc[f] == LBM_BC_PRESSURE && !(p->bc_rho[f][k] > 0)) return LBM_ERR_INVALID_ARG;
     }
     if (p->ncomp == 2 && p->g[0][1] != p->g[1][0]) return LBM_ERR_INVALID_ARG;
-    if (p->schedule != LBM_SCHEDULE_AUTO && p->schedule != LBM_SCHEDULE_TWO_PASS) return LBM_ERR_INVALID_ARG;
+    if (p->schedule != LBM_SCHEDULE_AUTO && p->schedule != LBM_SCHEDULE_TWO_PASS &&
+        p->schedule != LBM_SCHEDULE_SINGLE_PASS)
+        return LBM_ERR_INVALID_ARG;
     return LBM_OK;
 }
 
@@ -241,14 +243,42 @@ void fill_params(const lbm_ctx* c, Params<T>& P)
         P.sqrtT[k] = (T)std::sqrt(c->T[kk]);
         P.alpha[k] = (T)p->alpha[kk];
         {
-            const double b = p->eos_b[kk], RT = p->eos_R[kk] * c->T[kk];
-            const double att = p->eos[kk] == EOS_RK ? p->eos_a[kk] / std::sqrt(c->T[kk])
-                                                    : p->eos_a[kk] * eos_alpha(p->eos[kk], p->eos_omega[kk], p->T_red[kk]);
-            P.eos_b_lo[k] = (T)(b - (double)P.eos_b[k]);
-            P.RT_lo[k] = (T)(RT - (double)P.RT[k]);
-            P.att[k] = (T)att;
-            P.att_lo[k] = (T)(att - (double)P.att[k]);
+            // p = rho N(rho) / D(rho); coefficients of N in powers of rho
+            const double b = p->eos_b[kk], a = p->eos_a[kk], RT = p->eos_R[kk] * c->T[kk];
+            const double att = p->eos[kk] == EOS_RK ? a / std::sqrt(c->T[kk])
+                                                    : a * eos_alpha(p->eos[kk], p->eos_omega[kk], p->T_red[kk]);
+            double cf[5] = {0, 0, 0, 0, 0};
+            switch (p->eos[kk]) {
+            case EOS_CS: {  // N = RT (1 + e + e^2 - e^3) - a rho (1 - e)^3, e = b rho / 4
+                const double B = b / 4.0;
+                cf[0] = RT;
+                cf[1] = RT * B - a;
+                cf[2] = RT * B * B + 3.0 * a * B;
+                cf[3] = -RT * B * B * B - 3.0 * a * B * B;
+                cf[4] = a * B * B * B;
+                break;
+            }
+            case EOS_PR:  // N = RT (1 + 2 b rho - b^2 rho^2) - att rho (1 - b rho)
+                cf[0] = RT; cf[1] = 2.0 * b * RT - att; cf[2] = att * b - RT * b * b;
+                break;
+            case EOS_VDW:  // N = RT - a rho (1 - b rho)
+                cf[0] = RT; cf[1] = -a; cf[2] = a * b;
+                break;
+            default:  // RK, RKS: N = RT (1 + b rho) - att rho (1 - b rho)
+                cf[0] = RT; cf[1] = RT * b - att; cf[2] = att * b;
+                break;
+            }
+            for (int d = 0; d < 5; ++d) {
+                P.eos_c[k][d] = (T)cf[d];
+                P.eos_c_lo[k][d] = (T)(cf[d] - (double)P.eos_c[k][d]);
+            }
             P.alpha_lo[k] = (T)(p->alpha[kk] - (double)P.alpha[k]);
+            const double tg = p->g[kk][kk] != 0.0 ? 2.0 / p->g[kk][kk] : 0.0;
+            P.two_over_g[k] = (T)tg;
+            P.two_over_g_lo[k] = (T)(tg - (double)P.two_over_g[k]);
+            const double gm = -p->g[kk][kk] / 12.0;
+            P.gm12[k] = (T)gm;
+            P.gm12_lo[k] = (T)(gm - (double)P.gm12[k]);
         }
         P.A[k] = (T)p->A[kk];
         P.oneA[k] = (T)(1.0 - p->A[kk]);
@@ -318,7 +348,7 @@ cudaError_t fields_pass(lbm_ctx* c, const Params<T>& P)
 
 bool use_fused(const lbm_ctx* c)
 {
-    return c->prm.schedule == LBM_SCHEDULE_AUTO && c->D == 3 && !c->geom;
+    return c->prm.schedule == LBM_SCHEDULE_SINGLE_PASS && c->D == 3 && !c->geom;
 }
 
 template <typename T>

@@ -387,13 +387,13 @@ def test_single_pass_matches_two_pass_bitwise(variant):
         case, init = cases.droplet_3d_exp(shape=shape, radius=10.0)
         rhos = init["rho"]
     out = []
-    for sched in ("auto", "two_pass"):
+    for sched in ("single_pass", "two_pass"):
         lat = Lattice(dict(case, schedule=sched))
         for k, r in enumerate(rhos):
             lat.init_fields(k, r)
         lat.step(25)
         ms, n = lat.profile_step(3)
-        assert (n[0] == 0) == (sched == "auto")     # the single-pass kernel really ran
+        assert (n[0] == 0) == (sched == "single_pass")     # the single-pass kernel really ran
         out.append([lat.populations(k) for k in range(lat.K)])
     for a, b in zip(*out):
         assert torch.equal(a, b)
