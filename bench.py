@@ -307,7 +307,8 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload] if args.n == 256 else
                    WORKLOADS[args.workload].replace("256^3", "%d^3" % args.n), "shape": [nx, ny, nz], "components": K,
-                   "schedule": "single-pass" if fused else "two-pass",
+                   "schedule": "single-pass" if fused else (
+                       "slab-overlapped two-pass" if args.schedule == "slab_overlap" else "two-pass"),
                    "parallelism": "replicas" if world > 1 else "single-gpu",
                    "l2": "inputs larger than L2 (two %.2f GB population buffers)" % (
                        K * 19 * N * 4 / 1e9)},
@@ -338,7 +339,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="pr256", choices=sorted(WORKLOADS))
-    ap.add_argument("--schedule", default="auto", choices=["auto", "two_pass", "single_pass"])
+    ap.add_argument("--schedule", default="auto", choices=["auto", "two_pass", "single_pass", "slab_overlap"])
     ap.add_argument("--n", type=int, default=256, help="cube edge (256 = the benchmark workload; "
                     "smaller edges are for profiling captures)")
     ap.add_argument("--e2e-steps", type=int, default=200)

@@ -63,13 +63,18 @@ enum { LBM_EOS_CS = 0, LBM_EOS_PR = 1, LBM_EOS_VDW = 2, LBM_EOS_RK = 3, LBM_EOS_
  * (x faces only) */
 enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL = 1, LBM_BC_PRESSURE = 2 };
 enum { LBM_HOST = 0, LBM_DEVICE = 1 };
-/* kernel schedule of a step. TWO_PASS: a density pass (psi to HBM) and a collide pass.
+/* kernel schedule of a step. AUTO and TWO_PASS: a density pass (psi to HBM) and a collide
+ * pass, back to back. SLAB_OVERLAP (D3Q19 lattices of 64 or more planes without solids,
+ * else TWO_PASS): the same two passes over z slabs of about 32 planes, overlapped on two
+ * internal streams forked from and joined back to the caller's stream (the collide of a
+ * slab starts once the density of its neighbour slabs is done); on GB300 at 256^3 it
+ * measured 6% slower than TWO_PASS, because the collide pass already occupies every SM.
  * SINGLE_PASS (periodic D3Q19 lattices without solids only, else two passes): psi is
- * recomputed on chip from the populations, which are read and written once. AUTO =
- * TWO_PASS: on GB300 the accurate FP32 arithmetic makes the single pass's psi recompute
- * cost more issue slots than the HBM traffic it saves. All give the same values bit for
- * bit. */
-enum { LBM_SCHEDULE_AUTO = 0, LBM_SCHEDULE_TWO_PASS = 1, LBM_SCHEDULE_SINGLE_PASS = 2 };
+ * recomputed on chip from the populations, which are read and written once; on GB300 the
+ * accurate FP32 arithmetic makes that recompute cost more issue slots than the HBM traffic
+ * it saves. All give the same values bit for bit. */
+enum { LBM_SCHEDULE_AUTO = 0, LBM_SCHEDULE_TWO_PASS = 1, LBM_SCHEDULE_SINGLE_PASS = 2,
+       LBM_SCHEDULE_SLAB_OVERLAP = 3 };
 
 /*
  * Problem parameters (all per component k = 0, 1; entries of absent components are ignored).
@@ -118,7 +123,7 @@ typedef struct lbm_params {
     double body_accel[2][3];
     int bc[6];
     double bc_rho[6][2];
-    int schedule;    /* LBM_SCHEDULE_AUTO | LBM_SCHEDULE_TWO_PASS | LBM_SCHEDULE_SINGLE_PASS */
+    int schedule;    /* LBM_SCHEDULE_AUTO | _TWO_PASS | _SINGLE_PASS | _SLAB_OVERLAP */
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -178,8 +183,9 @@ lbm_status lbm_sync(lbm_ctx* ctx);
  * stream between the kernels of every step, then synchronise. ms[0], ms[1], ms[2]
  * receive the summed device time (milliseconds) of the density, virtual-density and
  * collide kernels; launches[0..2] the number of launches of each. Timing aid for the
- * benchmark; the arithmetic is that of lbm_step. With the single-pass schedule the
- * density slot stays 0 and the collide slot holds the single-pass kernel. */
+ * benchmark; the arithmetic is that of lbm_step. The kernels run back to back here (no
+ * slab overlap). With the single-pass schedule the density slot stays 0 and the collide
+ * slot holds the single-pass kernel. */
 lbm_status lbm_profile_step(lbm_ctx* ctx, int nsteps, double* ms, long long* launches);
 
 /* Number of kernels this context has launched since creation. */

@@ -78,6 +78,7 @@ struct KArgs {
     double* partials;    // [diag_blocks][8]
     double* totals;      // [8]
     int zchunk;          // z planes per CTA of the single-pass step (0 = default)
+    int z0, zcount;      // density / collide launches over planes [z0, z0 + zcount) (zcount 0 = all)
     cudaStream_t stream;
 };
 

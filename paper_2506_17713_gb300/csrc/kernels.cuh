@@ -235,12 +235,19 @@ LBM_HD T eos_denominator(const Params<T>& P, int k, T rho)
     }
 }
 
+template <int DEG, typename T>
+LBM_HD FF<T> eos_numerator(const Params<T>& P, int k, T rho)
+{
+    FF<T> n = {P.eos_c[k][DEG], P.eos_c_lo[k][DEG]};
+#pragma unroll
+    for (int d = DEG - 1; d >= 0; --d) n = ff_add(ff_mul(n, rho), FF<T>{P.eos_c[k][d], P.eos_c_lo[k][d]});
+    return n;
+}
+
 template <typename T>
 LBM_HD FF<T> eos_energy_ff(const Params<T>& P, int k, T rho)
 {
-    const int deg = P.eos[k] == EOS_CS ? 4 : 2;
-    FF<T> n = {P.eos_c[k][deg], P.eos_c_lo[k][deg]};
-    for (int d = deg - 1; d >= 0; --d) n = ff_add(ff_mul(n, rho), FF<T>{P.eos_c[k][d], P.eos_c_lo[k][d]});
+    const FF<T> n = P.eos[k] == EOS_CS ? eos_numerator<4>(P, k, rho) : eos_numerator<2>(P, k, rho);
     // alpha N / D: the quotient of hi + lo by a float, corrected once
     const FF<T> an = ff_mul(n, FF<T>{P.alpha[k], P.alpha_lo[k]});
     const T den = eos_denominator(P, k, rho);
@@ -295,11 +302,11 @@ struct Node {
     long long n;
 };
 
-__device__ __forceinline__ bool node_of_thread(int nx, int ny, Node& nd)
+__device__ __forceinline__ bool node_of_thread(int nx, int ny, Node& nd, int z0 = 0)
 {
     nd.x = blockIdx.x * blockDim.x + threadIdx.x;
     nd.y = blockIdx.y;
-    nd.z = blockIdx.z;
+    nd.z = blockIdx.z + z0;
     nd.n = (long long)nd.x + (long long)nx * ((long long)nd.y + (long long)ny * nd.z);
     return nd.x < nx;
 }
@@ -575,7 +582,7 @@ LBM_HD void interaction_force(const KArgs<T>& a, const Node& nd, const T (&rho)[
 {
     const Params<T>& P = a.p;
     const long long N = P.N;
-    const T* psi = a.psi;
+    const T* __restrict__ psi = a.psi;
     if (!GEOM) {
         // periodic: x + e from the wrapped offsets (index d + 1 of Wrap3 holds x - d)
         const Wrap3 w = wrap3(P, nd.x, nd.y, nd.z);
@@ -701,7 +708,9 @@ LBM_HD void collide(const Params<T>& P, int k, T (&f)[L::Q], T rho, const T (&u)
             });
             dm = dm * rho;
             constexpr double inv_norm = 1.0 / mrt_norm<L>(a);
-            if constexpr (L::conserved(a)) {
+            if constexpr (a == 0) {
+                m[a] = T(0);  // density: neither relaxed nor shifted (unused below)
+            } else if constexpr (L::conserved(a)) {
                 m[a] = dm * T(inv_norm);
             } else {
                 T acc = T(0);
@@ -732,7 +741,7 @@ LBM_HD void collide(const Params<T>& P, int k, T (&f)[L::Q], T rho, const T (&u)
             T acc = T(0);
             static_for<L::Q>([&](auto ac) {
                 constexpr int a = decltype(ac)::value;
-                constexpr int c = mrt_even<L>(a) ? L::M(a, 0) : 0;
+                constexpr int c = (a != 0 && mrt_even<L>(a)) ? L::M(a, 0) : 0;
                 if constexpr (c != 0) acc += T(c) * m[a];
             });
             relax[0] = acc;
@@ -742,7 +751,7 @@ LBM_HD void collide(const Params<T>& P, int k, T (&f)[L::Q], T rho, const T (&u)
             T ev = T(0), od = T(0);
             static_for<L::Q>([&](auto ac) {
                 constexpr int a = decltype(ac)::value;
-                constexpr int c = L::M(a, i);
+                constexpr int c = a == 0 ? 0 : L::M(a, i);
                 constexpr bool even = mrt_even<L>(a);
                 T& t = even ? ev : od;
                 if constexpr (c == 1) t += m[a];
@@ -772,7 +781,7 @@ template <class L, typename T, int K, bool GEOM>
 __global__ void __launch_bounds__(256) k_density(const KArgs<T> a)
 {
     Node nd;
-    if (!node_of_thread(a.p.nx, a.p.ny, nd)) return;
+    if (!node_of_thread(a.p.nx, a.p.ny, nd, a.z0)) return;
     if (GEOM && a.solid[nd.n]) return;
     const long long N = a.p.N;
     bool bad = false, clamp = false;
@@ -824,7 +833,7 @@ template <class L, typename T, int K, int COLL, bool GEOM>
 __global__ void __launch_bounds__(256) k_collide(const KArgs<T> a)
 {
     Node nd;
-    if (!node_of_thread(a.p.nx, a.p.ny, nd)) return;
+    if (!node_of_thread(a.p.nx, a.p.ny, nd, a.z0)) return;
     if (GEOM && a.solid[nd.n]) return;
     const Params<T>& P = a.p;
     const long long N = P.N;
@@ -1183,12 +1192,13 @@ template <class L, typename T, int K, int COLL, bool GEOM>
 cudaError_t run_k(int op, const KArgs<T>& a)
 {
     const dim3 b = node_block(a.p.nx), g = node_grid(a.p.nx, a.p.ny, a.p.nz, b);
+    const dim3 gz = node_grid(a.p.nx, a.p.ny, a.zcount > 0 ? a.zcount : a.p.nz, b);  // density / collide
     switch (op) {
-    case OP_DENSITY: k_density<L, T, K, GEOM><<<g, b, 0, a.stream>>>(a); break;
+    case OP_DENSITY: k_density<L, T, K, GEOM><<<gz, b, 0, a.stream>>>(a); break;
     case OP_VIRTUAL:
         if (a.n_bsolid > 0) k_virtual<L, T, K><<<(a.n_bsolid + 255) / 256, 256, 0, a.stream>>>(a);
         break;
-    case OP_COLLIDE: k_collide<L, T, K, COLL, GEOM><<<g, b, 0, a.stream>>>(a); break;
+    case OP_COLLIDE: k_collide<L, T, K, COLL, GEOM><<<gz, b, 0, a.stream>>>(a); break;
     case OP_FUSED:
         if constexpr (L::D == 3 && !GEOM) {
             constexpr int TX = 32, TY = 8;

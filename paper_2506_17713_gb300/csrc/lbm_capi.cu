@@ -44,6 +44,11 @@ struct lbm_ctx {
     double T[2];
     Params<float> pf;
     Params<double> pd;
+    // two-pass overlap: density slabs on sA, collide slabs on sB, forked from and
+    // joined back to the caller's stream every step
+    int nslab;
+    cudaStream_t sA, sB;
+    cudaEvent_t ev_fork, ev_join, ev_d[16];
 };
 
 // ---------------------------------------------------------------------------
@@ -187,7 +192,7 @@ lbm_status validate(const lbm_params* p)
     }
     if (p->ncomp == 2 && p->g[0][1] != p->g[1][0]) return LBM_ERR_INVALID_ARG;
     if (p->schedule != LBM_SCHEDULE_AUTO && p->schedule != LBM_SCHEDULE_TWO_PASS &&
-        p->schedule != LBM_SCHEDULE_SINGLE_PASS)
+        p->schedule != LBM_SCHEDULE_SINGLE_PASS && p->schedule != LBM_SCHEDULE_SLAB_OVERLAP)
         return LBM_ERR_INVALID_ARG;
     return LBM_OK;
 }
@@ -351,9 +356,48 @@ bool use_fused(const lbm_ctx* c)
     return c->prm.schedule == LBM_SCHEDULE_SINGLE_PASS && c->D == 3 && !c->geom;
 }
 
+// slabs of the overlapped two-pass step (0: run the two passes back to back)
+bool use_overlap(const lbm_ctx* c)
+{
+    return c->prm.schedule == LBM_SCHEDULE_SLAB_OVERLAP && c->nslab >= 2 && c->n_bsolid == 0 && c->sA && c->sB;
+}
+
+template <typename T>
+cudaError_t step_overlapped(lbm_ctx* c, const Params<T>& P)
+{
+    const int S = c->nslab, nz = c->prm.nz;
+    cudaError_t e = cudaEventRecord(c->ev_fork, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->sA, c->ev_fork, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->sB, c->ev_fork, 0);
+    KArgs<T> a = base_args<T>(c, P);
+    for (int s = 0; s < S && e == cudaSuccess; ++s) {
+        a.z0 = (int)((long long)s * nz / S);
+        a.zcount = (int)((long long)(s + 1) * nz / S) - a.z0;
+        a.stream = c->sA;
+        e = dispatch<T>(c, OP_DENSITY, a);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_d[s], c->sA);
+    }
+    // collide slab s reads psi of slabs s-1, s, s+1 (z wraps): slabs 1 .. S-1 in
+    // order, each after density slab min(s+1, S-1); slab 0 (needs slab S-1) last
+    for (int j = 0; j < S && e == cudaSuccess; ++j) {
+        const int s = j + 1 < S ? j + 1 : 0;
+        const int need = (s == 0 || s + 1 >= S) ? S - 1 : s + 1;
+        e = cudaStreamWaitEvent(c->sB, c->ev_d[need], 0);
+        a.z0 = (int)((long long)s * nz / S);
+        a.zcount = (int)((long long)(s + 1) * nz / S) - a.z0;
+        a.stream = c->sB;
+        if (e == cudaSuccess) e = dispatch<T>(c, OP_COLLIDE, a);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->sB);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    if (e == cudaSuccess) c->cur ^= 1;
+    return e;
+}
+
 template <typename T>
 cudaError_t step_once(lbm_ctx* c, const Params<T>& P)
 {
+    if (use_overlap(c)) return step_overlapped<T>(c, P);
     if (use_fused(c)) {
         KArgs<T> a = base_args<T>(c, P);
         const cudaError_t e = dispatch<T>(c, OP_FUSED, a);
@@ -482,6 +526,19 @@ lbm_status lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void
     if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, 256, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) { delete c; return LBM_ERR_CUDA; }
+    // slab-overlapped two-pass step: about 32 planes per slab, 2 to 16 slabs
+    c->nslab = 0;
+    if (p->schedule == LBM_SCHEDULE_SLAB_OVERLAP && c->D == 3 && p->nz >= 64) {
+        int S = p->nz / 32;
+        c->nslab = S < 2 ? 2 : (S > 16 ? 16 : S);
+        bool ok = cudaStreamCreateWithFlags(&c->sA, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&c->sB, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
+        for (int s = 0; ok && s < c->nslab; ++s)
+            ok = cudaEventCreateWithFlags(&c->ev_d[s], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) { lbm_destroy(c); return LBM_ERR_CUDA; }
+    }
     *out = c;
     return LBM_OK;
 }
@@ -801,7 +858,22 @@ lbm_status lbm_temperature(const lbm_ctx* c, int comp, double* T)
     return LBM_OK;
 }
 
-void lbm_destroy(lbm_ctx* c) { delete c; }
+void lbm_destroy(lbm_ctx* c)
+{
+    if (!c) return;
+    if (c->sA || c->sB) {
+        // outstanding work of the context must finish before its streams go
+        if (c->sB) cudaStreamSynchronize(c->sB);
+        if (c->sA) cudaStreamSynchronize(c->sA);
+    }
+    for (int s = 0; s < 16; ++s)
+        if (c->ev_d[s]) cudaEventDestroy(c->ev_d[s]);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->sA) cudaStreamDestroy(c->sA);
+    if (c->sB) cudaStreamDestroy(c->sB);
+    delete c;
+}
 
 const char* lbm_status_str(lbm_status s)
 {

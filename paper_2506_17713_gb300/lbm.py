@@ -268,7 +268,7 @@ def params_from_case(case):
     for f in range(6):
         for k in range(2):
             p.bc_rho[f][k] = float(br[f, k])
-    p.schedule = {"auto": 0, "two_pass": 1, "single_pass": 2}[case.get("schedule", "auto")]
+    p.schedule = {"auto": 0, "two_pass": 1, "single_pass": 2, "slab_overlap": 3}[case.get("schedule", "auto")]
     return p
 
 
