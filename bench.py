@@ -13,6 +13,7 @@ For N > 1 (torchrun) every rank advances its own lattice (independent
 replicas, weak scaling); ranks only meet at the timing barriers.
 """
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -66,6 +67,41 @@ def algorithmic_bytes(case, fused=False):
     collide = 2 * K * Q * e + K * e + (1 if geom else 0)
     density = K * Q * e + K * e + (K * e + 1 if geom else 0)
     return {"collide": collide, "density": density, "step": collide + density}
+
+
+KERNEL_SOURCES = ("args.h", "kernels.cuh", "lattice.cuh")
+
+
+def kernel_source_hash():
+    """sha256 over the sources that define the step kernels (order fixed)."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2506_17713_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def committed_traffic(kernel, workload, n):
+    """DRAM bytes per launch of `kernel` (dram__bytes_read.sum + dram__bytes_write.sum)
+    from the committed ncu summary of this workload, or None when there is none or the
+    kernel sources have changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic_%s_n%d.md" % (workload, n))
+    if not os.path.exists(path):
+        return None
+    digest, value = None, None
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("kernel sources sha256:"):
+                digest = line.split(":", 1)[1].strip()
+            cells = [c.strip() for c in line.strip().strip("|").split("|")]
+            if len(cells) >= 5 and cells[0].startswith(kernel + "<"):
+                try:
+                    value = int(cells[4])
+                except ValueError:
+                    pass
+    if digest != kernel_source_hash():
+        return None
+    return value
 
 
 def load_peaks():
@@ -314,7 +350,8 @@ def run_ours(args):
                        K * 19 * N * 4 / 1e9)},
         "roofline": {"bound": "hbm", "kernel": "k_fused" if fused else "k_collide", "achieved": round(ach_col, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(ach_col / peak, 4),
-                     "peak_kind": peak_kind, "traffic": None,
+                     "peak_kind": peak_kind,
+                     "traffic": committed_traffic("k_fused" if fused else "k_collide", args.workload, args.n),
                      "bytes_per_lu": abytes["collide"], "ms_per_launch": round(t_col * 1e3, 4),
                      "density_kernel": {"achieved": round(ach_den, 1), "frac": round(ach_den / peak, 4),
                                         "bytes_per_lu": abytes["density"],

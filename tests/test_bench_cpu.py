@@ -63,3 +63,17 @@ def test_reference_arm_json_line():
     assert line["impl"] == "reference" and line["unit"] == "MLUPS" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_committed_traffic_is_gated_by_kernel_source_hash(monkeypatch):
+    import bench
+    path = os.path.join(ROOT, "profiles", "dram_traffic_pr256_n256.md")
+    if not os.path.exists(path):
+        pytest.skip("no committed DRAM traffic summary")
+    digest = next(l.split(":", 1)[1].strip() for l in open(path) if l.startswith("kernel sources sha256:"))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: digest)
+    t = bench.committed_traffic("k_collide", "pr256", 256)
+    assert isinstance(t, int) and t > 0
+    assert bench.committed_traffic("k_collide", "pr256", 128) is None      # no summary for that size
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 64)
+    assert bench.committed_traffic("k_collide", "pr256", 256) is None      # kernels changed since the capture
