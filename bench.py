@@ -53,19 +53,22 @@ def make_case(name, n=256):
     return case, init
 
 
-def algorithmic_bytes(case, fused=False):
-    """Bytes each kernel must move per lattice update (DRAM, each value once).
-    Two-pass schedule -- collide: read K*Q populations + K psi [+ 1 B mask], write
-    K*Q populations; density: read K*Q populations [+ 1 B mask], write K psi [+ K rho
-    next to solids]. Single-pass schedule (k_fused): read and write K*Q populations."""
+def algorithmic_bytes(case, fused=False, fluid_list=False):
+    """Bytes each kernel must move per lattice update of one node it processes (DRAM,
+    each value once). Two-pass schedule -- collide: read K*Q populations + K psi
+    [+ 1 B mask], write K*Q populations; density: read K*Q populations [+ 1 B mask],
+    write K psi [+ K rho next to solids]. With solids the kernels run over the fluid-node
+    list: the units are fluid nodes and each also reads its 4 B list entry. Single-pass
+    schedule (k_fused): read and write K*Q populations."""
     Q = 19 if case["lattice"] == "D3Q19" else 9
     e = 8 if case.get("real") == "f64" else 4
     K = int(case.get("ncomp", 1))
-    geom = any(b != "periodic" for b in case.get("bc", ["periodic"] * 6))
+    geom = any(b != "periodic" for b in case.get("bc", ["periodic"] * 6)) or fluid_list
     if fused:
         return {"collide": 2 * K * Q * e, "density": 0, "step": 2 * K * Q * e}
-    collide = 2 * K * Q * e + K * e + (1 if geom else 0)
-    density = K * Q * e + K * e + (K * e + 1 if geom else 0)
+    lst = 4 if fluid_list else 0
+    collide = 2 * K * Q * e + K * e + (1 if geom else 0) + lst
+    density = K * Q * e + K * e + (K * e + 1 if geom else 0) + lst
     return {"collide": collide, "density": density, "step": collide + density}
 
 
@@ -289,13 +292,16 @@ def run_ours(args):
     # --- per-kernel device time (events between the kernels of every step)
     ms, cnt = lat.profile_step(args.steps)
     fused = cnt[0] == 0
-    abytes = algorithmic_bytes(case, fused)
+    solid = init.get("solid")
+    n_fluid = int(N - np.count_nonzero(solid)) if solid is not None else N
+    units = n_fluid if solid is not None and n_fluid < N else N   # nodes the two kernels process
+    abytes = algorithmic_bytes(case, fused, fluid_list=units < N)
     t_col = ms[2] / max(cnt[2], 1) / 1e3
     t_den = ms[0] / max(cnt[0], 1) / 1e3
     peak, peak_kind = load_peaks()
-    ach_col = abytes["collide"] * N / t_col / 1e9
-    ach_den = abytes["density"] * N / t_den / 1e9 if not fused else 0.0
-    step_gbs = abytes["step"] * N * args.steps / secs / 1e9
+    ach_col = abytes["collide"] * units / t_col / 1e9
+    ach_den = abytes["density"] * units / t_den / 1e9 if not fused else 0.0
+    step_gbs = abytes["step"] * units * args.steps / secs / 1e9
 
     # --- end to end through the C ABI with pinned host buffers
     e2e = None
@@ -346,13 +352,15 @@ def run_ours(args):
                    "schedule": "single-pass" if fused else (
                        "slab-overlapped two-pass" if args.schedule == "slab_overlap" else "two-pass"),
                    "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "fluid_nodes": n_fluid, "mflups": round(mlups * n_fluid / N, 1),
                    "l2": "inputs larger than L2 (two %.2f GB population buffers)" % (
                        K * 19 * N * 4 / 1e9)},
         "roofline": {"bound": "hbm", "kernel": "k_fused" if fused else "k_collide", "achieved": round(ach_col, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(ach_col / peak, 4),
                      "peak_kind": peak_kind,
                      "traffic": committed_traffic("k_fused" if fused else "k_collide", args.workload, args.n),
-                     "bytes_per_lu": abytes["collide"], "ms_per_launch": round(t_col * 1e3, 4),
+                     "bytes_per_lu": abytes["collide"], "units_per_launch": units,
+                     "ms_per_launch": round(t_col * 1e3, 4),
                      "density_kernel": {"achieved": round(ach_den, 1), "frac": round(ach_den / peak, 4),
                                         "bytes_per_lu": abytes["density"],
                                         "ms_per_launch": round(t_den * 1e3, 4)},

@@ -15,11 +15,42 @@ enum : int { COLL_BGK = 0, COLL_MRT = 1 };
 // status word slots (device int[8])
 enum : int { ST_UNSTABLE = 0, ST_PSI_CLAMP = 1, ST_TIMEOUT = 2 };
 
+// Exact unsigned 32-bit division by an invariant divisor d (Granlund & Montgomery,
+// "Division by invariant integers using multiplication", PLDI 1994, Fig. 4.1):
+// with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+//   n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0),  t = mulhi(m, n).
+struct FastDiv {
+    uint32_t d, m, s1, s2;
+};
+
+inline FastDiv make_fastdiv(uint32_t d)
+{
+    uint32_t l = 0;
+    while (l < 32 && (1ull << l) < d) ++l;
+    FastDiv f;
+    f.d = d;
+    f.m = (uint32_t)((((1ull << l) - d) << 32) / d + 1);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l > 1 ? l - 1 : 0;
+    return f;
+}
+
+__host__ __device__ __forceinline__ uint32_t fast_div(uint32_t n, const FastDiv& f)
+{
+#ifdef __CUDA_ARCH__
+    const uint32_t t = __umulhi(f.m, n);
+#else
+    const uint32_t t = (uint32_t)(((uint64_t)f.m * n) >> 32);
+#endif
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
 // Physical parameters in the compute type T, resolved on the host.
 template <typename T>
 struct Params {
     int nx, ny, nz;
     long long N;
+    FastDiv div_nx, div_ny;   // node index -> (x, y, z) for fluid-list kernels
     int ncomp;
     int collision;
     int common_velocity;
@@ -28,6 +59,7 @@ struct Params {
     int eos[2];
     T omega[2];          // 1 / tau
     T rates[2][19];      // MRT rates, stress = 1/tau, conserved = 0
+    T rates_n[2][19];    // rates[k][a] / |M_a|^2 (squared norm of moment row a)
     T eos_a[2], eos_b[2], RT[2], alphaT[2], sqrtT[2];
     T alpha_lo[2];                  // hi + lo parts for FP32
     T eos_c[2][5], eos_c_lo[2][5];  // p = rho N(rho) / D(rho): coefficients of N, hi + lo
@@ -63,6 +95,8 @@ struct KArgs {
     const uint8_t* solid;
     const int* bsolid;   // boundary-solid node list
     int n_bsolid;
+    const int* fluid;    // fluid node list (ascending), or null: kernels run over every node
+    int n_fluid;
     int geom;            // solids present or a non-periodic face
     int* status;         // device status word
     // operation-specific

@@ -311,6 +311,33 @@ __device__ __forceinline__ bool node_of_thread(int nx, int ny, Node& nd, int z0 
     return nd.x < nx;
 }
 
+// Node of this thread in the fluid-node list (lattices with solids): threads map
+// to fluid nodes in ascending index order, so solid nodes cost no lanes.
+template <typename T>
+__device__ __forceinline__ bool node_of_list(const KArgs<T>& a, Node& nd)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.n_fluid) return false;
+    const uint32_t n = (uint32_t)a.fluid[t];
+    const uint32_t yz = fast_div(n, a.p.div_nx);
+    const uint32_t z = fast_div(yz, a.p.div_ny);
+    nd.x = (int)(n - yz * (uint32_t)a.p.nx);
+    nd.y = (int)(yz - z * (uint32_t)a.p.ny);
+    nd.z = (int)z;
+    nd.n = (long long)n;
+    return true;
+}
+
+// Node of this thread: from the fluid list when there is one, else from the
+// (x, y, z) grid, skipping solid nodes.
+template <bool GEOM, typename T>
+__device__ __forceinline__ bool fluid_node(const KArgs<T>& a, Node& nd)
+{
+    if (GEOM && a.fluid) return node_of_list(a, nd);
+    if (!node_of_thread(a.p.nx, a.p.ny, nd, a.z0)) return false;
+    return !(GEOM && a.solid[nd.n]);
+}
+
 // Stencil neighbour x + e for the force and wetting stencils: periodic faces
 // wrap, other faces clamp the coordinate into the domain.
 template <bool GEOM, typename T>
@@ -441,19 +468,17 @@ LBM_HD void gather_k(const T* __restrict__ f_all, const Params<T>& P,
 {
     const T* fk = f_all + (long long)k * L::Q * P.N;
     const long long N = P.N;
-    if (!GEOM) {
+    if constexpr (!GEOM) {
         gather_periodic<L, T>(fk, N, wrap3(P, nd.x, nd.y, nd.z), f);
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        long long src;
-        const int kind = pull_source<GEOM>(P, solid, nd.x, nd.y, nd.z, L::ex(i), L::ey(i), L::ez(i), src);
-        if (kind == 0) f[i] = fk[(long long)i * N + src];
-        else if (kind == 1) f[i] = fk[(long long)L::opp(i) * N + nd.n];
-        else f[i] = T(0);
-    }
-    if (GEOM) {
+        for (int i = 0; i < L::Q; ++i) {
+            long long src;
+            const int kind = pull_source<GEOM>(P, solid, nd.x, nd.y, nd.z, L::ex(i), L::ey(i), L::ez(i), src);
+            if (kind == 0) f[i] = fk[(long long)i * N + src];
+            else if (kind == 1) f[i] = fk[(long long)L::opp(i) * N + nd.n];
+            else f[i] = T(0);
+        }
         if (nd.x == 0 && P.bc[0] == BC_PRESSURE) zou_he<L, T>(f, +1, P.bc_rho[0][k]);
         else if (nd.x == P.nx - 1 && P.bc[1] == BC_PRESSURE) zou_he<L, T>(f, -1, P.bc_rho[1][k]);
     }
@@ -517,18 +542,22 @@ LBM_HD constexpr int g_twelfths(int i)
 // w_kk = psi^k(x) + A_k delta^k (delta = mean of the two neighbours minus psi(x)),
 // w_kk' = (1 - A_k) psi^k(x) for k' != k. Hence
 //   F^k = -(1/12) [ psi^k(x) (g_kk S^k + (1 - A_k) sum_{k'!=k} g_kk' S^k') + A_k g_kk D^k ],
-//   S^k = sum_i c_i e_i dpsi^k (accumulated as hi + lo from exact differences),
-//   D^k = sum_i c_i e_i dpsi^k delta^k (small; plain accumulation).
+//   S^k = sum_i c_i e_i dpsi^k,
+//   D^k = sum_i c_i e_i dpsi^k delta^k (small; accumulated as 2 D^k).
+// dpsi is exact whenever the two neighbours lie within a factor of two of each
+// other (Sterbenz), which holds across any resolved interface; otherwise its
+// rounding is relative to a large difference. The products with psi(x) and g/12
+// are formed in double-float: their roundings land on F / rho every step.
 // psi_at(k, ex, ey, ez) returns psi^k at x + e (e = 0: at x itself).
 template <class L, typename T, int K, class PsiAt>
 LBM_HD void interaction_force_at(const Params<T>& P, const PsiAt& psi_at, const T (&rho)[K], T (&F)[K][3])
 {
-    T Sh[K][3], Sl[K][3], D[K][3], px[K];
+    T S[K][3], D[K][3], px[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         px[k] = psi_at(k, 0, 0, 0);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) Sh[k][d] = Sl[k][d] = D[k][d] = T(0);
+        for (int d = 0; d < 3; ++d) S[k][d] = D[k][d] = T(0);
     }
 #pragma unroll
     for (int i = 1; i < L::Q; ++i) {
@@ -538,12 +567,11 @@ LBM_HD void interaction_force_at(const Params<T>& P, const PsiAt& psi_at, const 
         for (int k = 0; k < K; ++k) {
             const T p1 = psi_at(k, L::ex(i), L::ey(i), L::ez(i));
             const T p2 = psi_at(k, -L::ex(i), -L::ey(i), -L::ez(i));
-            const FF<T> dp = ff_two_sum(p1, -p2);
-            const T dh = c * dp.hi, dl = c * dp.lo;               // c <= 4: exact
-            const T dd = dh * (T(0.5) * ((p1 - px[k]) + (p2 - px[k])));
-            if (L::ex(i)) { Sh[k][0] += L::ex(i) > 0 ? dh : -dh; Sl[k][0] += L::ex(i) > 0 ? dl : -dl; D[k][0] += L::ex(i) > 0 ? dd : -dd; }
-            if (L::ey(i)) { Sh[k][1] += L::ey(i) > 0 ? dh : -dh; Sl[k][1] += L::ey(i) > 0 ? dl : -dl; D[k][1] += L::ey(i) > 0 ? dd : -dd; }
-            if (L::ez(i)) { Sh[k][2] += L::ez(i) > 0 ? dh : -dh; Sl[k][2] += L::ez(i) > 0 ? dl : -dl; D[k][2] += L::ez(i) > 0 ? dd : -dd; }
+            const T dh = c * (p1 - p2);                            // c <= 4: exact
+            const T dd = dh * ((p1 - px[k]) + (p2 - px[k]));       // 2 dpsi delta
+            if (L::ex(i)) { S[k][0] += L::ex(i) > 0 ? dh : -dh; D[k][0] += L::ex(i) > 0 ? dd : -dd; }
+            if (L::ey(i)) { S[k][1] += L::ey(i) > 0 ? dh : -dh; D[k][1] += L::ey(i) > 0 ? dd : -dd; }
+            if (L::ez(i)) { S[k][2] += L::ez(i) > 0 ? dh : -dh; D[k][2] += L::ez(i) > 0 ? dd : -dd; }
         }
     }
 #pragma unroll
@@ -553,19 +581,17 @@ LBM_HD void interaction_force_at(const Params<T>& P, const PsiAt& psi_at, const 
             FF<T> v;
             if (K == 1) {
                 // F = (-g/12) (psi(x) S + A D)
-                const FF<T> S = ff_two_sum(Sh[k][d], Sl[k][d]);
-                v = ff_two_prod(px[k], S.hi);
-                v.lo = fma(px[k], S.lo, v.lo) + P.A[k] * D[k][d];
+                v = ff_two_prod(px[k], S[k][d]);
+                v.lo = fma(T(0.5) * P.A[k], D[k][d], v.lo);
             } else {
                 // g_kk S^k + (1 - A_k) sum_{k' != k} g_kk' S^k', times psi^k(x), + A_k g_kk D^k
-                FF<T> tot = ff_mul(ff_two_sum(Sh[k][d], Sl[k][d]), P.g[k][k]);
+                FF<T> tot = ff_mul(ff_of(S[k][d]), P.g[k][k]);
 #pragma unroll
                 for (int kp = 0; kp < K; ++kp) {
                     if (kp == k) continue;
-                    const FF<T> Sx = ff_two_sum(Sh[kp][d], Sl[kp][d]);
-                    tot = ff_add(tot, ff_mul(ff_mul(Sx, P.g[k][kp]), FF<T>{P.oneA[k], P.oneA_lo[k]}));
+                    tot = ff_add(tot, ff_mul(ff_mul(ff_of(S[kp][d]), P.g[k][kp]), FF<T>{P.oneA[k], P.oneA_lo[k]}));
                 }
-                v = ff_add(ff_mul(tot, px[k]), ff_of(P.A[k] * P.g[k][k] * D[k][d]));
+                v = ff_add(ff_mul(tot, px[k]), ff_of(T(0.5) * P.A[k] * P.g[k][k] * D[k][d]));
             }
             // times -1/12 (K = 1: times -g/12)
             const T ch = K == 1 ? P.gm12[k] : T(-1.0 / 12.0);
@@ -646,6 +672,119 @@ LBM_HD void feq_split(int i, T rho, const T (&u)[3], T uu, T& hi, T& lo)
     lo = fma(wr.hi, poly, fma(w_lo, rho, wr.lo));
 }
 
+// D3Q19 MRT collision with EDM forcing in factored form: the same update as the
+// generic moment-space path below (f* = f + M^-1 (Delta m^eq - S m^neq), d'Humieres
+// basis), with the transforms written through the sums that several moments share.
+//   Forward: even moments are combinations of the rest value n0, the axis-pair sums
+//   a_x, a_y, a_z and the edge-pair sums B_xy, B_xz, B_yz (plus xy/yz/xz differences
+//   of edge pairs); odd moments of the pair differences.
+//   EDM: Delta m^eq needs only rho du and the six rho dq_dd' (dq = u'u' - uu).
+//   Backward: the even part of a direction depends only on its class (axis x, y, z or
+//   edge plane), the odd part on the pair, so each pair gets ev +- od.
+// Non-equilibrium pair sums and differences come straight from f: with
+// f^eq_i = W (1 + poly_i) + L (W = w rho rounded, L its rounding error plus w_lo rho),
+// poly_{i,opp} = t +- 3 e.u and t = 4.5 (e.u)^2 - 1.5 u.u,
+//   neq_i + neq_opp = (f_i - W) + (f_opp - W) - 2 (W t + L)   (f - W exact)
+//   neq_i - neq_opp = (f_i - f_opp) - 6 W e.u                (f_i - f_opp exact)
+template <typename T>
+LBM_HD void collide_mrt_d3q19(const Params<T>& P, int k, T (&f)[19], T rho, const T (&u)[3], const T (&du)[3])
+{
+    constexpr double w_of[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};  // rest, axis, edge
+    const T m15uu = T(-1.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    T W[3], Lw[3], W6[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const T wh = T(w_of[c]), wl = T(w_of[c] - (double)T(w_of[c]));
+        const FF<T> wr = ff_two_prod(wh, rho);
+        W[c] = wr.hi;
+        Lw[c] = fma(wl, rho, wr.lo);
+        W6[c] = T(-6) * wr.hi;
+    }
+    const T n0 = (f[0] - W[0]) - fma(W[0], m15uu, Lw[0]);
+    // pair p = directions (2p+1, 2p+2): +x, +y, +z, +x+y, +x-y, +x+z, +x-z, +y+z, +y-z
+    const T eu[9] = {u[0], u[1], u[2], u[0] + u[1], u[0] - u[1], u[0] + u[2], u[0] - u[2], u[1] + u[2], u[1] - u[2]};
+    T ps[9], pd[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const int c = p < 3 ? 1 : 2;
+        const T fi = f[2 * p + 1], fo = f[2 * p + 2];
+        const T t = fma(T(4.5) * eu[p], eu[p], m15uu);
+        ps[p] = fma(T(-2), fma(W[c], t, Lw[c]), (fi - W[c]) + (fo - W[c]));
+        pd[p] = fma(W6[c], eu[p], fi - fo);
+    }
+    // forward transform (moment rows of the d'Humieres basis, unnormalised)
+    const T ayz = ps[1] + ps[2], A = ps[0] + ayz;
+    const T Bxy = ps[3] + ps[4], Bxz = ps[5] + ps[6], Byz = ps[7] + ps[8];
+    const T Bxyxz = Bxy + Bxz, B = Bxyxz + Byz;
+    const T m_e = fma(T(-11), A, fma(T(8), B, T(-30) * n0));       // 19 c^2 - 30
+    const T m_eps = fma(T(-4), A, fma(T(12), n0, B));               // (21 c^4 - 53 c^2 + 24) / 2
+    const T P9 = fma(T(2), ps[0], -ayz), Q9 = fma(T(-2), Byz, Bxyxz);
+    const T m_9 = P9 + Q9, m_10 = fma(T(-2), P9, Q9);                // 3x^2 - c^2, (3c^2 - 5)(...)
+    const T R11 = ps[1] - ps[2], S11 = Bxy - Bxz;
+    const T m_11 = R11 + S11, m_12 = fma(T(-2), R11, S11);          // y^2 - z^2, (3c^2 - 5)(...)
+    const T m_13 = ps[3] - ps[4], m_14 = ps[7] - ps[8], m_15 = ps[5] - ps[6];  // xy, yz, xz
+    const T X1 = pd[3] + pd[4], X2 = pd[5] + pd[6];
+    const T Y1 = pd[3] - pd[4], Y2 = pd[7] + pd[8];
+    const T Z1 = pd[5] - pd[6], Z2 = pd[7] - pd[8];
+    const T m_4 = fma(T(-4), pd[0], X1 + X2), m_16 = X1 - X2;       // (5c^2 - 9) x, (y^2 - z^2) x
+    const T m_6 = fma(T(-4), pd[1], Y1 + Y2), m_17 = Y2 - Y1;       // (5c^2 - 9) y, (z^2 - x^2) y
+    const T m_8 = fma(T(-4), pd[2], Z1 + Z2), m_18 = Z1 - Z2;       // (5c^2 - 9) z, (x^2 - y^2) z
+    // Delta m^eq: e 19 rho tr(dq), eps -5.5 rho tr(dq), j rho du, q -2/3 rho du,
+    // 3p_xx rho (2 dq_xx - dq_yy - dq_zz) and 3pi_xx -1/2 of it, p_ww rho (dq_yy - dq_zz)
+    // and pi_ww -1/2 of it, p_xy, p_yz, p_xz rho dq_xy, rho dq_yz, rho dq_xz
+    const T up[3] = {u[0] + du[0], u[1] + du[1], u[2] + du[2]};
+    const T dxx = fma(u[0], du[0], du[0] * up[0]), dyy = fma(u[1], du[1], du[1] * up[1]);
+    const T dzz = fma(u[2], du[2], du[2] * up[2]), dxy = fma(u[0], du[1], du[0] * up[1]);
+    const T dyz = fma(u[1], du[2], du[1] * up[2]), dxz = fma(u[0], du[2], du[0] * up[2]);
+    const T dyzs = dyy + dzz;
+    const T r_tr = rho * (dxx + dyzs), r_9 = rho * fma(T(2), dxx, -dyzs), r_11 = rho * (dyy - dzz);
+    const T* sn = P.rates_n[k];
+    // normalised m' = (Delta m^eq - s m^neq) / |M_a|^2
+    const T e_ = fma(-sn[1], m_e, T(19.0 / 2394.0) * r_tr);
+    const T eps_ = fma(-sn[2], m_eps, T(-5.5 / 252.0) * r_tr);
+    const T jx_ = T(0.1) * rho * du[0], jy_ = T(0.1) * rho * du[1], jz_ = T(0.1) * rho * du[2];
+    const T qx_ = fma(-sn[4], m_4, T(-1.0 / 60.0) * rho * du[0]);
+    const T qy_ = fma(-sn[6], m_6, T(-1.0 / 60.0) * rho * du[1]);
+    const T qz_ = fma(-sn[8], m_8, T(-1.0 / 60.0) * rho * du[2]);
+    const T p9_ = fma(-sn[9], m_9, T(1.0 / 36.0) * r_9);
+    const T p10_ = fma(-sn[10], m_10, T(-1.0 / 144.0) * r_9);
+    const T p11_ = fma(-sn[11], m_11, T(1.0 / 12.0) * r_11);
+    const T p12_ = fma(-sn[12], m_12, T(-1.0 / 48.0) * r_11);
+    const T p13_ = fma(-sn[13], m_13, T(0.25) * (rho * dxy));
+    const T p14_ = fma(-sn[14], m_14, T(0.25) * (rho * dyz));
+    const T p15_ = fma(-sn[15], m_15, T(0.25) * (rho * dxz));
+    const T p16_ = -sn[16] * m_16, p17_ = -sn[17] * m_17, p18_ = -sn[18] * m_18;
+    // backward transform M^T m'
+    f[0] = f[0] + fma(T(-30), e_, T(12) * eps_);
+    {
+        const T C = fma(T(-11), e_, T(-4) * eps_);
+        const T H = fma(T(-2), p10_, p9_), Wv = fma(T(-2), p12_, p11_);
+        const T Tyz = C - H;
+        const T ev[3] = {fma(T(2), H, C), Tyz + Wv, Tyz - Wv};
+        const T od[3] = {fma(T(-4), qx_, jx_), fma(T(-4), qy_, jy_), fma(T(-4), qz_, jz_)};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            f[2 * d + 1] = f[2 * d + 1] + (ev[d] + od[d]);
+            f[2 * d + 2] = f[2 * d + 2] + (ev[d] - od[d]);
+        }
+    }
+    {
+        const T E0 = fma(T(8), e_, eps_), K9 = p9_ + p10_, K11 = p11_ + p12_;
+        const T EK = E0 + K9;
+        const T b_xy = EK + K11, b_xz = EK - K11, b_yz = fma(T(-2), K9, E0);
+        const T Jx = jx_ + qx_, Jy = jy_ + qy_, Jz = jz_ + qz_;
+        const T ev[6] = {b_xy + p13_, b_xy - p13_, b_xz + p15_, b_xz - p15_, b_yz + p14_, b_yz - p14_};
+        const T od[6] = {(Jx + Jy) + (p16_ - p17_), (Jx - Jy) + (p16_ + p17_),
+                         (Jx + Jz) + (p18_ - p16_), (Jx - Jz) - (p16_ + p18_),
+                         (Jy + Jz) + (p17_ - p18_), (Jy - Jz) + (p17_ + p18_)};
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            f[2 * q + 7] = f[2 * q + 7] + (ev[q] + od[q]);
+            f[2 * q + 8] = f[2 * q + 8] + (ev[q] - od[q]);
+        }
+    }
+}
+
 // Collision and EDM forcing of one component at one node. The update is formed
 // as f_i + (small correction) so that only one rounding lands on f_i. BGK adds
 // the EDM shift per direction; MRT adds it in moment space together with the
@@ -653,6 +792,10 @@ LBM_HD void feq_split(int i, T rho, const T (&u)[3], T uu, T& hi, T& lo)
 template <class L, typename T, int COLL>
 LBM_HD void collide(const Params<T>& P, int k, T (&f)[L::Q], T rho, const T (&u)[3], const T (&du)[3])
 {
+    if constexpr (COLL != COLL_BGK && L::Q == 19) {
+        collide_mrt_d3q19<T>(P, k, f, rho, u, du);
+        return;
+    }
     const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     T neq[L::Q];
 #pragma unroll
@@ -781,8 +924,7 @@ template <class L, typename T, int K, bool GEOM>
 __global__ void __launch_bounds__(256) k_density(const KArgs<T> a)
 {
     Node nd;
-    if (!node_of_thread(a.p.nx, a.p.ny, nd, a.z0)) return;
-    if (GEOM && a.solid[nd.n]) return;
+    if (!fluid_node<GEOM>(a, nd)) return;
     const long long N = a.p.N;
     bool bad = false, clamp = false;
 #pragma unroll
@@ -830,11 +972,10 @@ __global__ void __launch_bounds__(256) k_virtual(const KArgs<T> a)
 }
 
 template <class L, typename T, int K, int COLL, bool GEOM>
-__global__ void __launch_bounds__(256) k_collide(const KArgs<T> a)
+__global__ void __launch_bounds__(256, K == 1 ? 4 : 0) k_collide(const KArgs<T> a)
 {
     Node nd;
-    if (!node_of_thread(a.p.nx, a.p.ny, nd, a.z0)) return;
-    if (GEOM && a.solid[nd.n]) return;
+    if (!fluid_node<GEOM>(a, nd)) return;
     const Params<T>& P = a.p;
     const long long N = P.N;
     T f[K][L::Q];
@@ -1192,13 +1333,18 @@ template <class L, typename T, int K, int COLL, bool GEOM>
 cudaError_t run_k(int op, const KArgs<T>& a)
 {
     const dim3 b = node_block(a.p.nx), g = node_grid(a.p.nx, a.p.ny, a.p.nz, b);
-    const dim3 gz = node_grid(a.p.nx, a.p.ny, a.zcount > 0 ? a.zcount : a.p.nz, b);  // density / collide
+    // density / collide: one thread per fluid node from the fluid list when there is
+    // one, else the (x, y, z) grid (a z range of it for slab schedules)
+    const bool list = GEOM && a.fluid;
+    const dim3 lb(256, 1, 1), lg((unsigned)((a.n_fluid > 0 ? a.n_fluid : 1) + 255) / 256, 1, 1);
+    const dim3 gz = list ? lg : node_grid(a.p.nx, a.p.ny, a.zcount > 0 ? a.zcount : a.p.nz, b);
+    const dim3 bz = list ? lb : b;
     switch (op) {
-    case OP_DENSITY: k_density<L, T, K, GEOM><<<gz, b, 0, a.stream>>>(a); break;
+    case OP_DENSITY: k_density<L, T, K, GEOM><<<gz, bz, 0, a.stream>>>(a); break;
     case OP_VIRTUAL:
         if (a.n_bsolid > 0) k_virtual<L, T, K><<<(a.n_bsolid + 255) / 256, 256, 0, a.stream>>>(a);
         break;
-    case OP_COLLIDE: k_collide<L, T, K, COLL, GEOM><<<gz, b, 0, a.stream>>>(a); break;
+    case OP_COLLIDE: k_collide<L, T, K, COLL, GEOM><<<gz, bz, 0, a.stream>>>(a); break;
     case OP_FUSED:
         if constexpr (L::D == 3 && !GEOM) {
             constexpr int TX = 32, TY = 8;

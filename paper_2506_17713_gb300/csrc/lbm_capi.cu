@@ -27,8 +27,10 @@ struct lbm_ctx {
     void* psi;
     void* rho;
     uint8_t* solid;
-    int* bsolid;
+    int* bsolid;            // boundary solids, then the fluid node list, in one N-int region
     int n_bsolid;
+    int* fluid;
+    int n_fluid;
     void* u_prev;
     int* status;
     double* partials;
@@ -151,6 +153,7 @@ lbm_status validate(const lbm_params* p)
     if (!p) return LBM_ERR_INVALID_ARG;
     if (p->lattice != LBM_D2Q9 && p->lattice != LBM_D3Q19) return LBM_ERR_INVALID_ARG;
     if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->ny > 65535 || p->nz > 65535) return LBM_ERR_INVALID_ARG;
+    if ((long long)p->nx * p->ny * p->nz >= (1LL << 31)) return LBM_ERR_INVALID_ARG;  // node index in int32
     if (p->lattice == LBM_D2Q9 && p->nz != 1) return LBM_ERR_INVALID_ARG;
     if (p->ncomp != 1 && p->ncomp != 2) return LBM_ERR_INVALID_ARG;
     if (p->real != LBM_FP32 && p->real != LBM_FP64) return LBM_ERR_INVALID_ARG;
@@ -226,6 +229,8 @@ void fill_params(const lbm_ctx* c, Params<T>& P)
     std::memset(&P, 0, sizeof(P));
     P.nx = p->nx; P.ny = p->ny; P.nz = p->nz;
     P.N = c->N;
+    P.div_nx = make_fastdiv((uint32_t)p->nx);
+    P.div_ny = make_fastdiv((uint32_t)p->ny);
     P.ncomp = p->ncomp;
     P.collision = p->collision == LBM_MRT ? COLL_MRT : COLL_BGK;
     P.common_velocity = p->velocity == LBM_UEQ_COMMON;
@@ -239,7 +244,10 @@ void fill_params(const lbm_ctx* c, Params<T>& P)
         for (int m = 0; m < 19; ++m) {
             const bool cons = d2 ? D2Q9::conserved(m) : D3Q19::conserved(m);
             const bool str = d2 ? D2Q9::stress(m) : D3Q19::stress(m);
-            P.rates[k][m] = cons ? T(0) : (str ? (T)(1.0 / p->tau[kk]) : (T)p->mrt_s[kk][m]);
+            const double s = cons ? 0.0 : (str ? 1.0 / p->tau[kk] : p->mrt_s[kk][m]);
+            const int norm = d2 ? (m < 9 ? mrt_norm<D2Q9>(m) : 1) : mrt_norm<D3Q19>(m);
+            P.rates[k][m] = (T)s;
+            P.rates_n[k][m] = (T)(s / norm);
         }
         P.eos_a[k] = (T)p->eos_a[kk];
         P.eos_b[k] = (T)p->eos_b[kk];
@@ -311,6 +319,8 @@ KArgs<T> base_args(lbm_ctx* c, const Params<T>& P)
     a.solid = c->solid;
     a.bsolid = c->bsolid;
     a.n_bsolid = c->n_bsolid;
+    a.fluid = c->any_solid ? c->fluid : nullptr;
+    a.n_fluid = c->any_solid ? c->n_fluid : 0;
     a.geom = c->geom;
     a.status = c->status;
     a.u_prev = (T*)c->u_prev;
@@ -359,7 +369,7 @@ bool use_fused(const lbm_ctx* c)
 // slabs of the overlapped two-pass step (0: run the two passes back to back)
 bool use_overlap(const lbm_ctx* c)
 {
-    return c->prm.schedule == LBM_SCHEDULE_SLAB_OVERLAP && c->nslab >= 2 && c->n_bsolid == 0 && c->sA && c->sB;
+    return c->prm.schedule == LBM_SCHEDULE_SLAB_OVERLAP && c->nslab >= 2 && !c->any_solid && c->sA && c->sB;
 }
 
 template <typename T>
@@ -561,11 +571,19 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* solid, int where)
         v = v ? 1 : 0;
         c->any_solid |= v;
     }
+    // boundary solids, then (with solids present) the fluid nodes in ascending order:
+    // at most N entries together
     std::vector<int> list;
     c->n_bsolid = c->D == 2 ? build_boundary_list<D2Q9>(c, h.data(), list)
                             : build_boundary_list<D3Q19>(c, h.data(), list);
+    c->n_fluid = 0;
+    if (c->any_solid)
+        for (long long n = 0; n < c->N; ++n)
+            if (!h[(size_t)n]) list.push_back((int)n);
+    c->n_fluid = (int)list.size() - c->n_bsolid;
+    c->fluid = c->bsolid + c->n_bsolid;
     e = cudaMemcpyAsync(c->solid, h.data(), (size_t)c->N, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess && c->n_bsolid > 0)
+    if (e == cudaSuccess && !list.empty())
         e = cudaMemcpyAsync(c->bsolid, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return fail_cuda(c, e);

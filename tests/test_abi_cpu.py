@@ -69,6 +69,7 @@ def test_workspace_size_layout(lib):
     dict(rho_lo=[2.0, 2.0], rho_hi=[1.0, 1.0]),
     dict(mrt_rates=[[2.5] * 19]),
     dict(T_red=[0.0, 0.0]),
+    dict(shape=(2048, 1024, 1024)),            # 2^31 nodes: node indices are 32-bit
 ])
 def test_rejects_invalid_parameters(lib, bad):
     from paper_2506_17713_gb300 import lbm

@@ -259,6 +259,30 @@ def test_almost_all_solid():
     assert abs(m[0] - rho[2, 2, 3] - rho[2, 2, 4]) < 1e-12
 
 
+def test_fluid_list_wide_lattice_scattered_solids():
+    # kernels run over the fluid-node list when solids exist: nx above one block
+    # width, odd ny and nz (node -> (x, y, z) by invariant division), half the nodes solid
+    shape = (300, 7, 5)
+    case = cases.base_case("D3Q19", shape, psi=["exp"], g=[[-1.5, 0], [0, -1.5]], real="f64",
+                           collision="MRT", wet_phi=[1.2, 1.2], rho_lo=[0.5, 0.5], rho_hi=[1.5, 1.5])
+    solid = random_solids(shape, 0.5, 73)
+    rho = random_field(shape, 0.8, 1.2, 74)
+    lat, orc = run_both(case, [rho], 30, solid=solid)
+    compare(lat, orc, TOL64)
+
+
+def test_all_solid_lattice():
+    shape = (9, 7, 5)
+    case = cases.base_case("D3Q19", shape, psi=["exp"], g=[[-1.5, 0], [0, -1.5]], real="f64")
+    from paper_2506_17713_gb300 import Lattice
+    lat = Lattice(case)
+    lat.set_geometry(np.ones((5, 7, 9), dtype=np.uint8))
+    lat.init_fields(0, random_field(shape, 0.8, 1.2, 75))
+    lat.step(5)
+    m, _ = lat.diagnostics()
+    assert m[0] == 0.0
+
+
 def test_rest_state_stays_at_rest():
     shape = (20, 18, 16)
     case = cases.droplets_3d_pr(shape=shape, count=1, rmin=3, rmax=3)[0]
