@@ -203,20 +203,32 @@ def aggregate(units_per_rank, seconds_per_rank_max, world):
 # Reference arm: the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------
 
-def oracle_sample(case, init, steps):
-    """Time `steps` oracle steps on the full lattice; returns (MLUPS, seconds, threads)."""
+def oracle_sample(case, init, steps=None, seconds=None):
+    """Time oracle steps on the given lattice; returns (MLUPS, seconds, threads, steps).
+    With `seconds`, one untimed warm-up step and one timed step size the sample to about
+    that much CPU time."""
     import oracle
     s = oracle.OracleSim(case)
     if init.get("solid") is not None:
         s.set_geometry(init["solid"])
     for k, r in enumerate(init["rho"]):
         s.init_fields(k, r)
+    dt = 0.0
+    if seconds is not None:
+        s.step(1)                                  # untimed: threads start, pages fault in
+        t0 = time.perf_counter()
+        s.step(1)
+        dt = time.perf_counter() - t0
+        steps = int(min(1000, max(1, round(seconds / max(dt, 1e-6)))))
+        steps_left = steps - 1
+    else:
+        steps_left = steps
     t0 = time.perf_counter()
-    s.step(steps)
-    dt = time.perf_counter() - t0
+    s.step(steps_left)
+    dt += time.perf_counter() - t0
     K = int(case.get("ncomp", 1))
     nx, ny, nz = case["shape"]
-    return K * nx * ny * nz * steps / dt / 1e6, dt, oracle.threads()
+    return K * nx * ny * nz * steps / dt / 1e6, dt, oracle.threads(), steps
 
 
 def run_reference(args):
@@ -225,8 +237,8 @@ def run_reference(args):
         return
     case, init = make_case(args.workload, args.n)
     steps = max(1, min(args.steps, args.ref_steps))
-    mlups_w, _, _ = oracle_sample(case, init, 1)                 # warm-up (page-in)
-    mlups, dt, threads = oracle_sample(case, init, steps)
+    oracle_sample(case, init, 1)                                  # warm-up (page-in)
+    mlups, dt, threads, _ = oracle_sample(case, init, steps)
     nx, ny, nz = case["shape"]
     sample = "%d oracle steps on the full %dx%dx%d lattice (FP64, OpenMP)" % (steps, nx, ny, nz)
     line = {
@@ -337,9 +349,9 @@ def run_ours(args):
             if init.get("solid") is not None:
                 cinit["solid"] = init["solid"][:32]
             what = "a %dx%dx32 slab (first 32 z planes, periodic in z) of the lattice" % (nx, ny)
-        cpu_mlups, cpu_dt, threads = oracle_sample(ccase, cinit, args.cpu_steps)
+        cpu_mlups, cpu_dt, threads, csteps = oracle_sample(ccase, cinit, seconds=args.cpu_seconds)
         cpu = {"value": round(cpu_mlups, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
-               "sample": "%d FP64 oracle steps on %s (%.1f s)" % (args.cpu_steps, what, cpu_dt)}
+               "sample": "%d FP64 oracle steps on %s (%.1f s, after one untimed step)" % (csteps, what, cpu_dt)}
 
     line = {
         "metric": "D3Q19 Shan-Chen MLUPS", "value": round(mlups, 1), "unit": "MLUPS",
@@ -388,7 +400,8 @@ def main():
     ap.add_argument("--n", type=int, default=256, help="cube edge (256 = the benchmark workload; "
                     "smaller edges are for profiling captures)")
     ap.add_argument("--e2e-steps", type=int, default=200)
-    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="CPU time of the oracle sample behind cpu_baseline")
     ap.add_argument("--ref-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
