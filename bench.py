@@ -34,6 +34,19 @@ WORKLOADS = {
 }
 
 
+# populations as stored; compute is FP32 except for f64
+STORAGE = {"f32": "f32", "f64": "f64", "f16s": "f16 deviations f_i - w_i rho_ref",
+           "bf16s": "bf16 deviations f_i - w_i rho_ref"}
+
+
+def ref_density(workload):
+    """Default reference density of 16-bit storage: the vapour coexistence density of
+    the droplet workloads (vapour populations are then stored almost exactly and liquid
+    ones round relative to their own size), 1 (the lattice weights) otherwise."""
+    from synth import cases
+    return {"pr256": cases.COEX[("PR", 0.6)][0], "exp256": cases.EXP_COEX[0]}.get(workload, 1.0)
+
+
 def make_case(name, n=256):
     from synth import cases
     if name == "pr256":
@@ -61,14 +74,15 @@ def algorithmic_bytes(case, fused=False, fluid_list=False):
     list: the units are fluid nodes and each also reads its 4 B list entry. Single-pass
     schedule (k_fused): read and write K*Q populations."""
     Q = 19 if case["lattice"] == "D3Q19" else 9
-    e = 8 if case.get("real") == "f64" else 4
+    e = 8 if case.get("real") == "f64" else 4                       # scalars (psi, rho)
+    ep = 2 if case.get("real") in ("f16s", "bf16s") else e          # stored populations
     K = int(case.get("ncomp", 1))
     geom = any(b != "periodic" for b in case.get("bc", ["periodic"] * 6)) or fluid_list
     if fused:
-        return {"collide": 2 * K * Q * e, "density": 0, "step": 2 * K * Q * e}
+        return {"collide": 2 * K * Q * ep, "density": 0, "step": 2 * K * Q * ep}
     lst = 4 if fluid_list else 0
-    collide = 2 * K * Q * e + K * e + (1 if geom else 0) + lst
-    density = K * Q * e + K * e + (K * e + 1 if geom else 0) + lst
+    collide = 2 * K * Q * ep + K * e + (1 if geom else 0) + lst
+    density = K * Q * ep + K * e + (K * e + 1 if geom else 0) + lst
     return {"collide": collide, "density": density, "step": collide + density}
 
 
@@ -267,6 +281,11 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     case, init = make_case(args.workload, args.n)
     case["schedule"] = args.schedule
+    if args.real != "f32":
+        case["real"] = args.real
+        if args.real in ("f16s", "bf16s"):
+            rr = args.rho_ref if args.rho_ref is not None else ref_density(args.workload)
+            case["rho_ref"] = [rr, rr]
     nx, ny, nz = case["shape"]
     K = int(case.get("ncomp", 1))
     N = nx * ny * nz
@@ -357,7 +376,7 @@ def run_ours(args):
         "metric": "D3Q19 Shan-Chen MLUPS", "value": round(mlups, 1), "unit": "MLUPS",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * secs_max / args.steps, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if case.get("real") != "f64" else "f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if case.get("real") == "f64" else "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload] if args.n == 256 else
                    WORKLOADS[args.workload].replace("256^3", "%d^3" % args.n), "shape": [nx, ny, nz], "components": K,
@@ -365,8 +384,10 @@ def run_ours(args):
                        "slab-overlapped two-pass" if args.schedule == "slab_overlap" else "two-pass"),
                    "parallelism": "replicas" if world > 1 else "single-gpu",
                    "fluid_nodes": n_fluid, "mflups": round(mlups * n_fluid / N, 1),
+                   "storage": STORAGE[case.get("real", "f32")] + (
+                       " (rho_ref %.6g)" % case["rho_ref"][0] if "rho_ref" in case else ""),
                    "l2": "inputs larger than L2 (two %.2f GB population buffers)" % (
-                       K * 19 * N * 4 / 1e9)},
+                       K * 19 * N * (2 if case.get("real") in ("f16s", "bf16s") else 4) / 1e9)},
         "roofline": {"bound": "hbm", "kernel": "k_fused" if fused else "k_collide", "achieved": round(ach_col, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(ach_col / peak, 4),
                      "peak_kind": peak_kind,
@@ -397,6 +418,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="pr256", choices=sorted(WORKLOADS))
     ap.add_argument("--schedule", default="auto", choices=["auto", "two_pass", "single_pass", "slab_overlap"])
+    ap.add_argument("--real", default="f32", choices=["f32", "f64", "f16s", "bf16s"],
+                    help="population storage (f16s / bf16s: 16-bit deviations, FP32 compute)")
+    ap.add_argument("--rho-ref", type=float, default=None,
+                    help="reference density of 16-bit storage (default: per workload)")
     ap.add_argument("--n", type=int, default=256, help="cube edge (256 = the benchmark workload; "
                     "smaller edges are for profiling captures)")
     ap.add_argument("--e2e-steps", type=int, default=200)

@@ -26,7 +26,11 @@
  *   - No exception crosses the ABI. A context is not thread safe.
  *   - Errors are sticky: after a CUDA error or a detected instability every later
  *     call on the context returns the same status until it is destroyed.
- *   - Stored precision (LBM_FP32 / LBM_FP64) is also the compute precision.
+ *   - Precision: LBM_FP32 and LBM_FP64 store and compute in that type. LBM_FP16S and
+ *     LBM_BF16S compute in FP32 and store each population as the 16-bit (FP16 / BF16)
+ *     deviation f_i - w_i rho_ref[k] from the lattice weights times a reference density,
+ *     rounded to nearest. This halves the bytes of a step. The global mass and momentum sums
+ *     and the residual stay FP64 in every mode.
  */
 #ifndef GB300_LBM_H
 #define GB300_LBM_H
@@ -49,7 +53,7 @@ typedef enum {
 } lbm_status;
 
 enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };
-enum { LBM_FP32 = 0, LBM_FP64 = 1 };
+enum { LBM_FP32 = 0, LBM_FP64 = 1, LBM_FP16S = 2, LBM_BF16S = 3 };
 enum { LBM_BGK = 0, LBM_MRT = 1 };
 /* equilibrium velocity of a component: its own bare velocity j^k / rho^k
  * (Eq. macroeq_mcp) or the Shan-Chen common velocity sum_k j^k/tau_k / sum_k rho^k/tau_k */
@@ -107,7 +111,7 @@ typedef struct lbm_params {
     int lattice;     /* LBM_D2Q9 | LBM_D3Q19 */
     int nx, ny, nz;  /* nz = 1 for D2Q9 */
     int ncomp;       /* 1 | 2 */
-    int real;        /* LBM_FP32 | LBM_FP64 */
+    int real;        /* LBM_FP32 | LBM_FP64 | LBM_FP16S | LBM_BF16S */
     int collision;   /* LBM_BGK | LBM_MRT */
     int velocity;    /* LBM_UEQ_COMPONENT | LBM_UEQ_COMMON */
     double tau[2];
@@ -124,6 +128,8 @@ typedef struct lbm_params {
     int bc[6];
     double bc_rho[6][2];
     int schedule;    /* LBM_SCHEDULE_AUTO | _TWO_PASS | _SINGLE_PASS | _SLAB_OVERLAP */
+    double rho_ref[2]; /* LBM_FP16S / LBM_BF16S: reference density of the stored deviation
+                          f_i - w_i rho_ref[k] (1 = the lattice weights); ignored otherwise */
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -155,7 +161,7 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
 
 /* Density and velocity u = (sum_i f_i e_i + F/2) / rho of component comp, or of the
  * mixture (sum over components) for comp = -1, at the current time (Eq. after Eq. edm).
- * Element type = the context's real type (float for LBM_FP32, double for LBM_FP64).
+ * Element type = the context's compute type (double for LBM_FP64, float otherwise).
  * rho: [N], u: [D][N]; either may be NULL; solids give 0. */
 lbm_status lbm_macroscopic(lbm_ctx* ctx, int comp, void* rho, void* u, int where);
 
@@ -167,9 +173,12 @@ lbm_status lbm_macroscopic(lbm_ctx* ctx, int comp, void* rho, void* u, int where
  * non-finite or non-positive density. */
 lbm_status lbm_diagnostics(lbm_ctx* ctx, double* mass, double* momentum, double* residual);
 
-/* Post-stream populations of component comp, [Q][N] of the real type (checkpoint /
+/* Post-stream populations of component comp, [Q][N] of the compute type (checkpoint /
  * inspection). lbm_set_populations restores them exactly (bit for bit), except for the
- * populations that constant-density faces recompute. */
+ * populations that constant-density faces recompute. With 16-bit storage the values are
+ * the stored deviations plus w_i rho_ref in FP32, and lbm_set_populations rounds
+ * f_i - w_i rho_ref back to the storage type (the values lbm_get_populations returned
+ * round back to the stored bits). */
 lbm_status lbm_get_populations(lbm_ctx* ctx, int comp, void* f, int where);
 lbm_status lbm_set_populations(lbm_ctx* ctx, int comp, const void* f, int where);
 
@@ -209,7 +218,8 @@ const char* lbm_status_str(lbm_status s);
  *
  *   p     lattice parameters; lattice, nx, ny, nz, ncomp and real are used.
  *   d_f   device pointer, post-stream populations [ncomp][Q][N] of the real type of p,
- *         the layout lbm_get_populations writes (solid nodes hold 0).
+ *         the layout lbm_get_populations writes (solid nodes hold 0). Only LBM_FP32 and
+ *         LBM_FP64 are accepted (LBM_ERR_INVALID_ARG for the 16-bit storage modes).
  *   mass  host pointer, ncomp doubles: sum over nodes of sum_i f_i, per component, summed
  *         in FP64 in a fixed order.
  *   stream  cudaStream_t (NULL = legacy default stream); the call synchronises it.

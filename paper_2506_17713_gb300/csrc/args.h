@@ -3,6 +3,8 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace lbm {
@@ -69,6 +71,7 @@ struct Params {
     T oneA[2], oneA_lo[2];   // 1 - A as hi + lo
     T wet_phi[2], wet_drho[2], rho_min[2], rho_max[2];
     T accel[2][3];
+    T rho_ref[2];        // 16-bit population storage holds f_i - w_i rho_ref[k] (0 otherwise)
     T bc_rho[2][2];      // [x side][component]
 };
 
@@ -88,8 +91,8 @@ enum : int {
 template <typename T>
 struct KArgs {
     Params<T> p;
-    const T* f_src;      // pre-stream (post-collision) populations, [K][Q][N]
-    T* f_dst;            // next pre-stream buffer
+    const void* f_src;   // pre-stream (post-collision) populations, [K][Q][N] of the storage type
+    void* f_dst;         // next pre-stream buffer
     T* psi;              // [K][N]
     T* rho;              // [K][N] (read by the virtual-density pass)
     const uint8_t* solid;
@@ -119,7 +122,9 @@ struct KArgs {
 constexpr int DIAG_BLOCKS = 1024;
 constexpr int DIAG_THREADS = 256;
 
-template <class L, typename T>
+// T: compute type; S: population storage type (T itself, or __half / __nv_bfloat16
+// holding shifted values for T = float)
+template <class L, typename T, typename S>
 cudaError_t run(int op, const KArgs<T>& a);
 
 }  // namespace lbm

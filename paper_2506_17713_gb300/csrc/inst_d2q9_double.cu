@@ -3,5 +3,5 @@
 #include "kernels.cuh"
 
 namespace lbm {
-template cudaError_t run<D2Q9, double>(int op, const KArgs<double>& a);
+template cudaError_t run<D2Q9, double, double>(int op, const KArgs<double>& a);
 }  // namespace lbm

@@ -3,5 +3,5 @@
 #include "kernels.cuh"
 
 namespace lbm {
-template cudaError_t run<D2Q9, float>(int op, const KArgs<float>& a);
+template cudaError_t run<D2Q9, float, float>(int op, const KArgs<float>& a);
 }  // namespace lbm

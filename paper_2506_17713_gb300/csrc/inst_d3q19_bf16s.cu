@@ -1,0 +1,7 @@
+// Kernel instantiations for the D3Q19 lattice: FP32 compute, BF16 shifted population
+// storage (one translation unit per lattice and type, compiled in parallel).
+#include "kernels.cuh"
+
+namespace lbm {
+template cudaError_t run<D3Q19, float, __nv_bfloat16>(int op, const KArgs<float>& a);
+}  // namespace lbm

@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 #include <utility>
 
 #include "args.h"
@@ -262,12 +263,14 @@ LBM_HD FF<T> eos_energy_ff(const Params<T>& P, int k, T rho)
 
 // psi^k (and the pseudopotential energy U^k = alpha p_EOS - c_s^2 rho) from rho^k.
 // Returns true when the square-root argument 2U/g was negative (psi clamped to 0).
-template <typename T>
+// EXACT = false (16-bit population storage, whose rounding is ~2^-11 or coarser)
+// evaluates the EOS in plain FP32.
+template <bool EXACT = true, typename T>
 LBM_HD bool pseudopotential(const Params<T>& P, int k, T rho, T& psi, T& U)
 {
     const T g = P.g[k][k];
     if (P.psi_kind[k] == PSI_EOS) {
-        if (sizeof(T) == 4) {
+        if (EXACT && sizeof(T) == 4) {
             const FF<T> u = eos_energy_ff(P, k, rho);
             const FF<T> arg = ff_mul(u, FF<T>{P.two_over_g[k], P.two_over_g_lo[k]});
             U = u.hi + u.lo;
@@ -291,6 +294,40 @@ LBM_HD bool pseudopotential(const Params<T>& P, int k, T rho, T& psi, T& U)
     psi = P.psi_kind[k] == PSI_RHO ? rho : exp(T(-1) / rho);
     U = T(0.5) * g * psi * psi;
     return false;
+}
+
+// ---------------------------------------------------------------------------
+// Population storage
+// ---------------------------------------------------------------------------
+//
+// S = T stores the populations themselves. A 16-bit S (FP16 or BF16, FP32
+// compute) stores the deviation f_i - w_i rho_ref of component k, rounded to
+// nearest; a load adds w_i rho_ref back in FP32.
+
+LBM_HD float pop_to_float(__half v) { return __half2float(v); }
+LBM_HD float pop_to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename S>
+LBM_HD S pop_from_float(float v);
+template <>
+LBM_HD __half pop_from_float<__half>(float v) { return __float2half_rn(v); }
+template <>
+LBM_HD __nv_bfloat16 pop_from_float<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+template <typename T, typename S>
+constexpr bool pop_shifted = !std::is_same<T, S>::value;
+
+template <class L, typename T, typename S>
+LBM_HD T load_pop(const S* __restrict__ p, long long m, int i, T rho_ref)
+{
+    if constexpr (pop_shifted<T, S>) return pop_to_float(p[m]) + T(L::w(i)) * rho_ref;
+    else return p[m];
+}
+
+template <class L, typename T, typename S>
+LBM_HD void store_pop(S* __restrict__ p, long long m, int i, T v, T rho_ref)
+{
+    if constexpr (pop_shifted<T, S>) p[m] = pop_from_float<S>(v - T(L::w(i)) * rho_ref);
+    else p[m] = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -449,39 +486,125 @@ LBM_HD Wrap3 wrap3(const Params<T>& P, int x, int y, int z)
     return w;
 }
 
-template <class L, typename T>
-LBM_HD void gather_periodic(const T* __restrict__ fk, long long N, const Wrap3& w, T (&f)[L::Q])
+// Per-node neighbour table for every lattice: for each axis the index offsets of the
+// coordinates c+1, c, c-1 (index 0, 1, 2, the convention of Wrap3). Periodic axes wrap.
+// Across a closed face (wall or constant density) the coordinate is clamped to c, and
+// 2 bits of fl record the face kind of that side (1 = wall, 2 = constant density):
+// bits [4a, 4a+2) for c+1 leaving through the max face of axis a, [4a+2, 4a+4) for
+// c-1 leaving through the min face.
+//   pull source of direction e:         offsets [e + 1], face bits of side e + 1
+//   force / wetting neighbour x + e:    offsets [1 - e]  (clamped, Section 2.5 stencils)
+struct Geo3 {
+    int xo[3], yo[3], zo[3];
+    unsigned fl;
+};
+
+template <bool GEOM, typename T>
+LBM_HD Geo3 geo3(const Params<T>& P, int x, int y, int z)
 {
+    Geo3 g;
+    g.fl = 0u;
+    if constexpr (!GEOM) {
+        const Wrap3 w = wrap3(P, x, y, z);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            g.xo[d] = w.xo[d];
+            g.yo[d] = w.yo[d];
+            g.zo[d] = w.zo[d];
+        }
+    } else {
+        const int c[3] = {x, y, z}, n[3] = {P.nx, P.ny, P.nz};
+        const int stride[3] = {1, P.nx, P.nx * P.ny};
+        int* o[3] = {g.xo, g.yo, g.zo};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int bmin = P.bc[2 * a], bmax = P.bc[2 * a + 1];
+            o[a][1] = c[a] * stride[a];
+            if (c[a] + 1 < n[a]) {
+                o[a][0] = (c[a] + 1) * stride[a];
+            } else if (bmax == BC_PERIODIC) {
+                o[a][0] = 0;
+            } else {
+                o[a][0] = c[a] * stride[a];
+                g.fl |= (bmax == BC_PRESSURE ? 2u : 1u) << (4 * a);
+            }
+            if (c[a] > 0) {
+                o[a][2] = (c[a] - 1) * stride[a];
+            } else if (bmin == BC_PERIODIC) {
+                o[a][2] = (n[a] - 1) * stride[a];
+            } else {
+                o[a][2] = c[a] * stride[a];
+                g.fl |= (bmin == BC_PRESSURE ? 2u : 1u) << (4 * a + 2);
+            }
+        }
+    }
+    return g;
+}
+
+// face bits met by the pull source of direction (ex, ey, ez)
+LBM_HD unsigned pull_face(const Geo3& g, int ex, int ey, int ez)
+{
+    unsigned f = 0u;
+    if (ex) f |= g.fl >> (ex > 0 ? 2 : 0);
+    if (ey) f |= g.fl >> (ey > 0 ? 6 : 4);
+    if (ez) f |= g.fl >> (ez > 0 ? 10 : 8);
+    return f & 3u;
+}
+
+// index of the force / wetting stencil neighbour x + e
+LBM_HD int stencil_index(const Geo3& g, int ex, int ey, int ez)
+{
+    return g.xo[1 - ex] + g.yo[1 - ey] + g.zo[1 - ez];
+}
+
+// Post-stream populations of components k0 .. k0+K-1 at a fluid node (Eq. lbe_steps
+// with halfway bounce-back): the pull decision of each direction -- regular source,
+// bounce-back at a wall face or solid node, or unknown across a constant-density face
+// (completed by Zou-He) -- is taken once and applied to every component.
+template <class L, typename T, typename S, int K, bool GEOM>
+LBM_HD void gather_all(const void* f_all, const Params<T>& P, const uint8_t* __restrict__ solid,
+                       const Node& nd, const Geo3& g, T (&f)[K][L::Q], int k0 = 0)
+{
+    const long long N = P.N;
+    const S* fs = static_cast<const S*>(f_all) + (long long)k0 * L::Q * N;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        const int src = w.xo[L::ex(i) + 1] + w.yo[L::ey(i) + 1] + w.zo[L::ez(i) + 1];
-        f[i] = fk[(long long)i * N + src];
+        const int src = g.xo[L::ex(i) + 1] + g.yo[L::ey(i) + 1] + g.zo[L::ez(i) + 1];
+        if constexpr (!GEOM) {
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                f[k][i] = load_pop<L, T, S>(fs, ((long long)k * L::Q + i) * N + src, i, P.rho_ref[k0 + k]);
+        } else {
+            const unsigned face = i == 0 ? 0u : pull_face(g, L::ex(i), L::ey(i), L::ez(i));
+            const bool unknown = (face & 2u) != 0u;   // constant-density x face (precedence)
+            const bool bounce = !unknown && (face == 1u || (i != 0 && solid[src]));
+            const long long m = bounce ? (long long)L::opp(i) * N + nd.n : (long long)i * N + src;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const T v = load_pop<L, T, S>(fs, (long long)k * L::Q * N + m, i, P.rho_ref[k0 + k]);
+                f[k][i] = unknown ? T(0) : v;
+            }
+        }
+    }
+    if constexpr (GEOM) {
+        if (P.bc[0] == BC_PRESSURE && nd.x == 0) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) zou_he<L, T>(f[k], +1, P.bc_rho[0][k0 + k]);
+        } else if (P.bc[1] == BC_PRESSURE && nd.x == P.nx - 1) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) zou_he<L, T>(f[k], -1, P.bc_rho[1][k0 + k]);
+        }
     }
 }
 
-// Post-stream populations of component k at a fluid node (pull + bounce-back +
-// constant-density faces).
-template <class L, typename T, bool GEOM>
-LBM_HD void gather_k(const T* __restrict__ f_all, const Params<T>& P,
-                                         const uint8_t* __restrict__ solid, const Node& nd, int k,
-                                         T (&f)[L::Q])
+template <class L, typename T, typename S, bool GEOM>
+LBM_HD void gather_k(const void* f_all, const Params<T>& P, const uint8_t* __restrict__ solid, const Node& nd,
+                     int k, T (&f)[L::Q])
 {
-    const T* fk = f_all + (long long)k * L::Q * P.N;
-    const long long N = P.N;
-    if constexpr (!GEOM) {
-        gather_periodic<L, T>(fk, N, wrap3(P, nd.x, nd.y, nd.z), f);
-    } else {
+    T fk[1][L::Q];
+    gather_all<L, T, S, 1, GEOM>(f_all, P, solid, nd, geo3<GEOM>(P, nd.x, nd.y, nd.z), fk, k);
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) {
-            long long src;
-            const int kind = pull_source<GEOM>(P, solid, nd.x, nd.y, nd.z, L::ex(i), L::ey(i), L::ez(i), src);
-            if (kind == 0) f[i] = fk[(long long)i * N + src];
-            else if (kind == 1) f[i] = fk[(long long)L::opp(i) * N + nd.n];
-            else f[i] = T(0);
-        }
-        if (nd.x == 0 && P.bc[0] == BC_PRESSURE) zou_he<L, T>(f, +1, P.bc_rho[0][k]);
-        else if (nd.x == P.nx - 1 && P.bc[1] == BC_PRESSURE) zou_he<L, T>(f, -1, P.bc_rho[1][k]);
-    }
+    for (int i = 0; i < L::Q; ++i) f[i] = fk[0][i];
 }
 
 // rho = sum_i f_i as a balanced tree over opposite-pair sums (rounding error grows
@@ -549,7 +672,8 @@ LBM_HD constexpr int g_twelfths(int i)
 // rounding is relative to a large difference. The products with psi(x) and g/12
 // are formed in double-float: their roundings land on F / rho every step.
 // psi_at(k, ex, ey, ez) returns psi^k at x + e (e = 0: at x itself).
-template <class L, typename T, int K, class PsiAt>
+// EXACT = false (16-bit population storage) assembles F in plain FP32.
+template <class L, typename T, int K, bool EXACT = true, class PsiAt>
 LBM_HD void interaction_force_at(const Params<T>& P, const PsiAt& psi_at, const T (&rho)[K], T (&F)[K][3])
 {
     T S[K][3], D[K][3], px[K];
@@ -573,6 +697,26 @@ LBM_HD void interaction_force_at(const Params<T>& P, const PsiAt& psi_at, const 
             if (L::ey(i)) { S[k][1] += L::ey(i) > 0 ? dh : -dh; D[k][1] += L::ey(i) > 0 ? dd : -dd; }
             if (L::ez(i)) { S[k][2] += L::ez(i) > 0 ? dh : -dh; D[k][2] += L::ez(i) > 0 ? dd : -dd; }
         }
+    }
+    if constexpr (!EXACT) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                T v;
+                if (K == 1) {
+                    v = P.gm12[k] * fma(px[k], S[k][d], T(0.5) * P.A[k] * D[k][d]);
+                } else {
+                    T tot = P.g[k][k] * S[k][d];
+#pragma unroll
+                    for (int kp = 0; kp < K; ++kp)
+                        if (kp != k) tot = fma(P.oneA[k] * P.g[k][kp], S[kp][d], tot);
+                    v = T(-1.0 / 12.0) * fma(tot, px[k], T(0.5) * P.A[k] * P.g[k][k] * D[k][d]);
+                }
+                F[k][d] = fma(rho[k], P.accel[k][d], v);
+            }
+        }
+        return;
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -602,27 +746,17 @@ LBM_HD void interaction_force_at(const Params<T>& P, const PsiAt& psi_at, const 
     }
 }
 
-// psi read from the global psi array (two-pass step, macroscopic outputs)
-template <class L, typename T, int K, bool GEOM>
-LBM_HD void interaction_force(const KArgs<T>& a, const Node& nd, const T (&rho)[K], T (&F)[K][3])
+// psi read from the global psi array (two-pass step, macroscopic outputs); the
+// neighbours come from the node's table g (wrapped, or clamped across closed faces)
+template <class L, typename T, int K, bool EXACT = true>
+LBM_HD void interaction_force(const KArgs<T>& a, const Node& nd, const Geo3& g, const T (&rho)[K], T (&F)[K][3])
 {
-    const Params<T>& P = a.p;
-    const long long N = P.N;
+    const long long N = a.p.N;
     const T* __restrict__ psi = a.psi;
-    if (!GEOM) {
-        // periodic: x + e from the wrapped offsets (index d + 1 of Wrap3 holds x - d)
-        const Wrap3 w = wrap3(P, nd.x, nd.y, nd.z);
-        auto at = [&](int k, int ex, int ey, int ez) -> T {
-            return psi[(long long)k * N + (w.xo[1 - ex] + w.yo[1 - ey] + w.zo[1 - ez])];
-        };
-        interaction_force_at<L, T, K>(P, at, rho, F);
-        return;
-    }
     auto at = [&](int k, int ex, int ey, int ez) -> T {
-        const long long m = (ex | ey | ez) ? stencil_nb<GEOM>(P, nd.x, nd.y, nd.z, ex, ey, ez) : nd.n;
-        return psi[(long long)k * N + m];
+        return psi[(long long)k * N + stencil_index(g, ex, ey, ez)];
     };
-    interaction_force_at<L, T, K>(P, at, rho, F);
+    interaction_force_at<L, T, K, EXACT>(a.p, at, rho, F);
 }
 
 // ---------------------------------------------------------------------------
@@ -920,20 +1054,20 @@ LBM_HD bool bad_density(T r)
     return !(r > T(0)) || !(r < T(1e30));
 }
 
-template <class L, typename T, int K, bool GEOM>
-__global__ void __launch_bounds__(256) k_density(const KArgs<T> a)
+template <class L, typename T, typename S, int K, bool GEOM>
+__global__ void __launch_bounds__(256, K == 1 ? 0 : 5) k_density(const KArgs<T> a)
 {
     Node nd;
     if (!fluid_node<GEOM>(a, nd)) return;
     const long long N = a.p.N;
     bool bad = false, clamp = false;
+    T f[K][L::Q];
+    gather_all<L, T, S, K, GEOM>(a.f_src, a.p, a.solid, nd, geo3<GEOM>(a.p, nd.x, nd.y, nd.z), f);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        T f[L::Q];
-        gather_k<L, T, GEOM>(a.f_src, a.p, a.solid, nd, k, f);
-        const T r = density<L, T>(f);
+        const T r = density<L, T>(f[k]);
         T ps, U;
-        clamp |= pseudopotential(a.p, k, r, ps, U);
+        clamp |= pseudopotential<!pop_shifted<T, S>>(a.p, k, r, ps, U);
         a.psi[(long long)k * N + nd.n] = ps;
         if (GEOM) a.rho[(long long)k * N + nd.n] = r;
         bad |= bad_density(r);
@@ -971,8 +1105,8 @@ __global__ void __launch_bounds__(256) k_virtual(const KArgs<T> a)
     }
 }
 
-template <class L, typename T, int K, int COLL, bool GEOM>
-__global__ void __launch_bounds__(256, K == 1 ? 4 : 0) k_collide(const KArgs<T> a)
+template <class L, typename T, typename S, int K, int COLL, bool GEOM>
+__global__ void __launch_bounds__(256, K == 1 ? 4 : 3) k_collide(const KArgs<T> a)
 {
     Node nd;
     if (!fluid_node<GEOM>(a, nd)) return;
@@ -980,13 +1114,22 @@ __global__ void __launch_bounds__(256, K == 1 ? 4 : 0) k_collide(const KArgs<T> 
     const long long N = P.N;
     T f[K][L::Q];
     T rho[K], j[K][3];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        gather_k<L, T, GEOM>(a.f_src, P, a.solid, nd, k, f[k]);
-        moments<L, T>(f[k], rho[k], j[k]);
-    }
     T F[K][3];
-    interaction_force<L, T, K, GEOM>(a, nd, rho, F);
+    if constexpr (GEOM) {
+        // lattices with solids or closed faces: one table for the pull and the force stencil
+        const Geo3 g = geo3<GEOM>(P, nd.x, nd.y, nd.z);
+        gather_all<L, T, S, K, GEOM>(a.f_src, P, a.solid, nd, g, f);
+#pragma unroll
+        for (int k = 0; k < K; ++k) moments<L, T>(f[k], rho[k], j[k]);
+        interaction_force<L, T, K, !pop_shifted<T, S>>(a, nd, g, rho, F);
+    } else {
+        // periodic: the wrapped offsets are cheap to form again, which keeps them out of
+        // the registers live across the moments (64 per thread here)
+        gather_all<L, T, S, K, GEOM>(a.f_src, P, a.solid, nd, geo3<GEOM>(P, nd.x, nd.y, nd.z), f);
+#pragma unroll
+        for (int k = 0; k < K; ++k) moments<L, T>(f[k], rho[k], j[k]);
+        interaction_force<L, T, K, !pop_shifted<T, S>>(a, nd, geo3<GEOM>(P, nd.x, nd.y, nd.z), rho, F);
+    }
     T uc[3] = {T(0), T(0), T(0)};
     if (K > 1 && P.common_velocity) {
         T den = T(0);
@@ -1009,9 +1152,9 @@ __global__ void __launch_bounds__(256, K == 1 ? 4 : 0) k_collide(const KArgs<T> 
             du[d] = F[k][d] * inv;
         }
         collide<L, T, COLL>(P, k, f[k], rho[k], u, du);
-        T* dst = a.f_dst + (long long)k * L::Q * N + nd.n;
+        S* dst = static_cast<S*>(a.f_dst) + (long long)k * L::Q * N + nd.n;
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) dst[(long long)i * N] = f[k][i];
+        for (int i = 0; i < L::Q; ++i) store_pop<L, T, S>(dst, (long long)i * N, i, f[k][i], P.rho_ref[k]);
     }
 }
 
@@ -1029,20 +1172,20 @@ __global__ void __launch_bounds__(256, K == 1 ? 4 : 0) k_collide(const KArgs<T> 
 // the Q populations (152 B in FP32) instead of the two-pass 236 B. The
 // arithmetic is that of the two-pass kernels, value for value.
 
-template <class L, typename T, int K>
+template <class L, typename T, typename S, int K>
 LBM_HD void psi_of_node(const KArgs<T>& a, int x, int y, int z, T (&out)[K])
 {
     Node nd{x, y, z, (long long)x + (long long)a.p.nx * ((long long)y + (long long)a.p.ny * z)};
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         T f[L::Q];
-        gather_k<L, T, false>(a.f_src, a.p, nullptr, nd, k, f);
+        gather_k<L, T, S, false>(a.f_src, a.p, nullptr, nd, k, f);
         T U;
-        pseudopotential(a.p, k, density<L, T>(f), out[k], U);
+        pseudopotential<!pop_shifted<T, S>>(a.p, k, density<L, T>(f), out[k], U);
     }
 }
 
-template <class L, typename T, int K, int COLL, int TX, int TY>
+template <class L, typename T, typename S, int K, int COLL, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY) k_fused(const KArgs<T> a, int zchunk)
 {
     static_assert(L::D == 3, "the z march needs a 3-D lattice");
@@ -1062,7 +1205,7 @@ __global__ void __launch_bounds__(TX * TY) k_fused(const KArgs<T> a, int zchunk)
     auto plane = [&](int zp, int slot) {
         const int zw = wrap(zp, nz);
         T v[K];
-        psi_of_node<L, T, K>(a, wrap(x0 + tx, nx), wrap(y0 + ty, ny), zw, v);
+        psi_of_node<L, T, S, K>(a, wrap(x0 + tx, nx), wrap(y0 + ty, ny), zw, v);
 #pragma unroll
         for (int k = 0; k < K; ++k) ring[slot][k][(ty + 1) * HX + tx + 1] = v[k];
         for (int h = tid; h < NH; h += TX * TY) {
@@ -1072,7 +1215,7 @@ __global__ void __launch_bounds__(TX * TY) k_fused(const KArgs<T> a, int zchunk)
             else if (h < 2 * HX + TY) { hx = -1; hy = h - 2 * HX; }
             else { hx = TX; hy = h - 2 * HX - TY; }
             const int xw = wrap(x0 + hx, nx), yw = wrap(y0 + hy, ny);
-            psi_of_node<L, T, K>(a, xw, yw, zw, v);
+            psi_of_node<L, T, S, K>(a, xw, yw, zw, v);
 #pragma unroll
             for (int k = 0; k < K; ++k) ring[slot][k][(hy + 1) * HX + hx + 1] = v[k];
         }
@@ -1092,7 +1235,7 @@ __global__ void __launch_bounds__(TX * TY) k_fused(const KArgs<T> a, int zchunk)
             bool bad = false;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                gather_k<L, T, false>(a.f_src, P, nullptr, nd, k, f[k]);
+                gather_k<L, T, S, false>(a.f_src, P, nullptr, nd, k, f[k]);
                 moments<L, T>(f[k], rho[k], j[k]);
                 bad |= bad_density(rho[k]);
             }
@@ -1102,7 +1245,7 @@ __global__ void __launch_bounds__(TX * TY) k_fused(const KArgs<T> a, int zchunk)
                 return ring[slot][k][(ty + 1 + ey) * HX + tx + 1 + ex];
             };
             T F[K][3];
-            interaction_force_at<L, T, K>(P, at, rho, F);
+            interaction_force_at<L, T, K, !pop_shifted<T, S>>(P, at, rho, F);
             T uc[3] = {T(0), T(0), T(0)};
             if (K > 1 && P.common_velocity) {
                 T den = T(0);
@@ -1125,9 +1268,9 @@ __global__ void __launch_bounds__(TX * TY) k_fused(const KArgs<T> a, int zchunk)
                     du[d] = F[k][d] * inv;
                 }
                 collide<L, T, COLL>(P, k, f[k], rho[k], u, du);
-                T* dst = a.f_dst + (long long)k * L::Q * N + nd.n;
+                S* dst = static_cast<S*>(a.f_dst) + (long long)k * L::Q * N + nd.n;
 #pragma unroll
-                for (int i = 0; i < L::Q; ++i) dst[(long long)i * N] = f[k][i];
+                for (int i = 0; i < L::Q; ++i) store_pop<L, T, S>(dst, (long long)i * N, i, f[k][i], P.rho_ref[k]);
             }
             if (bad) atomicAdd(a.status + ST_UNSTABLE, 1);
         }
@@ -1139,17 +1282,19 @@ __global__ void __launch_bounds__(TX * TY) k_fused(const KArgs<T> a, int zchunk)
 // written into the pre-stream buffer so that the next gather reproduces them:
 // f*_i(y) = F_i(y + e_i) for a regular link, F_opp(i)(y) where y + e_i is solid or
 // a wall, F_i(y) (unused) across a constant-density face.
-template <class L, typename T, bool GEOM, bool EQ>
+template <class L, typename T, typename S, bool GEOM, bool EQ>
 __global__ void __launch_bounds__(256) k_unstream(const KArgs<T> a)
 {
     Node nd;
     if (!node_of_thread(a.p.nx, a.p.ny, nd)) return;
     const Params<T>& P = a.p;
     const long long N = P.N;
-    T* dst = a.f_dst + (long long)a.comp * L::Q * N + nd.n;
-    if (GEOM && a.solid[nd.n]) {
+    const T rr = P.rho_ref[a.comp];
+    S* dst = static_cast<S*>(a.f_dst) + (long long)a.comp * L::Q * N + nd.n;
+    if (GEOM && a.solid[nd.n]) {   // never read; stored as zero deviation
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) dst[(long long)i * N] = T(0);
+        for (int i = 0; i < L::Q; ++i)
+            store_pop<L, T, S>(dst, (long long)i * N, i, pop_shifted<T, S> ? T(L::w(i)) * rr : T(0), rr);
         return;
     }
     auto value = [&](int i, long long m) -> T {
@@ -1172,11 +1317,11 @@ __global__ void __launch_bounds__(256) k_unstream(const KArgs<T> a)
         if (kind == 0) v = value(i, t);
         else if (kind == 1) v = value(L::opp(i), nd.n);
         else v = value(i, nd.n);
-        dst[(long long)i * N] = v;
+        store_pop<L, T, S>(dst, (long long)i * N, i, v, rr);
     }
 }
 
-template <class L, typename T, bool GEOM>
+template <class L, typename T, typename S, bool GEOM>
 __global__ void __launch_bounds__(256) k_get_pops(const KArgs<T> a)
 {
     Node nd;
@@ -1187,26 +1332,25 @@ __global__ void __launch_bounds__(256) k_get_pops(const KArgs<T> a)
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) f[i] = T(0);
     } else {
-        gather_k<L, T, GEOM>(a.f_src, a.p, a.solid, nd, a.comp, f);
+        gather_k<L, T, S, GEOM>(a.f_src, a.p, a.solid, nd, a.comp, f);
     }
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) a.out_f[(long long)i * N + nd.n] = f[i];
 }
 
 // rho and u = (j + F/2) / rho of one component or of the mixture at one node
-template <class L, typename T, int K, bool GEOM>
+template <class L, typename T, typename S, int K, bool GEOM>
 LBM_HD void node_macro(const KArgs<T>& a, const Node& nd, int comp, T& r_out,
                                            T (&u_out)[3], T (&rk)[K], T (&mk)[K][3])
 {
-    T f[L::Q];
+    const Geo3 g = geo3<GEOM>(a.p, nd.x, nd.y, nd.z);
+    T f[K][L::Q];
     T j[K][3];
+    gather_all<L, T, S, K, GEOM>(a.f_src, a.p, a.solid, nd, g, f);
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        gather_k<L, T, GEOM>(a.f_src, a.p, a.solid, nd, k, f);
-        moments<L, T>(f, rk[k], j[k]);
-    }
+    for (int k = 0; k < K; ++k) moments<L, T>(f[k], rk[k], j[k]);
     T F[K][3];
-    interaction_force<L, T, K, GEOM>(a, nd, rk, F);
+    interaction_force<L, T, K, !pop_shifted<T, S>>(a, nd, g, rk, F);
     T r = T(0), m[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -1222,7 +1366,7 @@ LBM_HD void node_macro(const KArgs<T>& a, const Node& nd, int comp, T& r_out,
     for (int d = 0; d < 3; ++d) u_out[d] = m[d] / r;
 }
 
-template <class L, typename T, int K, bool GEOM>
+template <class L, typename T, typename S, int K, bool GEOM>
 __global__ void __launch_bounds__(256) k_macro(const KArgs<T> a)
 {
     Node nd;
@@ -1231,7 +1375,7 @@ __global__ void __launch_bounds__(256) k_macro(const KArgs<T> a)
     T r = T(0), u[3] = {T(0), T(0), T(0)};
     if (!(GEOM && a.solid[nd.n])) {
         T rk[K], mk[K][3];
-        node_macro<L, T, K, GEOM>(a, nd, a.comp, r, u, rk, mk);
+        node_macro<L, T, S, K, GEOM>(a, nd, a.comp, r, u, rk, mk);
     }
     if (a.out_rho) a.out_rho[nd.n] = r;
     if (a.out_u)
@@ -1266,7 +1410,7 @@ __device__ __forceinline__ void block_sum8(double (&v)[8], double* out)
 // Partial sums per block (fixed grid, grid-stride in node order):
 // [0..1] mass per component, [2..7] momentum per component (j + F/2) -- or, in
 // residual mode, [0] sum |u - u_prev|^2 and [1] sum |u|^2 of the mixture velocity.
-template <class L, typename T, int K, bool GEOM>
+template <class L, typename T, typename S, int K, bool GEOM>
 __global__ void __launch_bounds__(DIAG_THREADS) k_diag(const KArgs<T> a)
 {
     const Params<T>& P = a.p;
@@ -1281,7 +1425,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag(const KArgs<T> a)
         nd.z = (int)(n / ((long long)P.nx * P.ny));
         if (GEOM && a.solid[n]) continue;
         T r, u[3], rk[K], mk[K][3];
-        node_macro<L, T, K, GEOM>(a, nd, -1, r, u, rk, mk);
+        node_macro<L, T, S, K, GEOM>(a, nd, -1, r, u, rk, mk);
         if (a.want_residual) {
             double du2 = 0.0, uu = 0.0;
 #pragma unroll
@@ -1329,7 +1473,7 @@ static __global__ void k_diag_final(const double* __restrict__ partials, double*
 inline dim3 node_block(int nx) { return dim3(nx >= 256 ? 256 : ((nx + 31) / 32) * 32, 1, 1); }
 inline dim3 node_grid(int nx, int ny, int nz, dim3 b) { return dim3((nx + b.x - 1) / b.x, ny, nz); }
 
-template <class L, typename T, int K, int COLL, bool GEOM>
+template <class L, typename T, typename S, int K, int COLL, bool GEOM>
 cudaError_t run_k(int op, const KArgs<T>& a)
 {
     const dim3 b = node_block(a.p.nx), g = node_grid(a.p.nx, a.p.ny, a.p.nz, b);
@@ -1340,28 +1484,28 @@ cudaError_t run_k(int op, const KArgs<T>& a)
     const dim3 gz = list ? lg : node_grid(a.p.nx, a.p.ny, a.zcount > 0 ? a.zcount : a.p.nz, b);
     const dim3 bz = list ? lb : b;
     switch (op) {
-    case OP_DENSITY: k_density<L, T, K, GEOM><<<gz, bz, 0, a.stream>>>(a); break;
+    case OP_DENSITY: k_density<L, T, S, K, GEOM><<<gz, bz, 0, a.stream>>>(a); break;
     case OP_VIRTUAL:
         if (a.n_bsolid > 0) k_virtual<L, T, K><<<(a.n_bsolid + 255) / 256, 256, 0, a.stream>>>(a);
         break;
-    case OP_COLLIDE: k_collide<L, T, K, COLL, GEOM><<<gz, bz, 0, a.stream>>>(a); break;
+    case OP_COLLIDE: k_collide<L, T, S, K, COLL, GEOM><<<gz, bz, 0, a.stream>>>(a); break;
     case OP_FUSED:
         if constexpr (L::D == 3 && !GEOM) {
             constexpr int TX = 32, TY = 8;
             const int zc = a.zchunk > 0 ? a.zchunk : 32;
             const dim3 fb(TX, TY, 1);
             const dim3 fg((a.p.nx + TX - 1) / TX, (a.p.ny + TY - 1) / TY, (a.p.nz + zc - 1) / zc);
-            k_fused<L, T, K, COLL, TX, TY><<<fg, fb, 0, a.stream>>>(a, zc);
+            k_fused<L, T, S, K, COLL, TX, TY><<<fg, fb, 0, a.stream>>>(a, zc);
         } else {
             return cudaErrorInvalidValue;
         }
         break;
-    case OP_INIT_EQ: k_unstream<L, T, GEOM, true><<<g, b, 0, a.stream>>>(a); break;
-    case OP_SET_POPS: k_unstream<L, T, GEOM, false><<<g, b, 0, a.stream>>>(a); break;
-    case OP_GET_POPS: k_get_pops<L, T, GEOM><<<g, b, 0, a.stream>>>(a); break;
-    case OP_MACRO: k_macro<L, T, K, GEOM><<<g, b, 0, a.stream>>>(a); break;
+    case OP_INIT_EQ: k_unstream<L, T, S, GEOM, true><<<g, b, 0, a.stream>>>(a); break;
+    case OP_SET_POPS: k_unstream<L, T, S, GEOM, false><<<g, b, 0, a.stream>>>(a); break;
+    case OP_GET_POPS: k_get_pops<L, T, S, GEOM><<<g, b, 0, a.stream>>>(a); break;
+    case OP_MACRO: k_macro<L, T, S, K, GEOM><<<g, b, 0, a.stream>>>(a); break;
     case OP_DIAG:
-        k_diag<L, T, K, GEOM><<<DIAG_BLOCKS, DIAG_THREADS, 0, a.stream>>>(a);
+        k_diag<L, T, S, K, GEOM><<<DIAG_BLOCKS, DIAG_THREADS, 0, a.stream>>>(a);
         k_diag_final<<<1, 32, 0, a.stream>>>(a.partials, a.totals);
         break;
     default: return cudaErrorInvalidValue;
@@ -1369,17 +1513,18 @@ cudaError_t run_k(int op, const KArgs<T>& a)
     return cudaGetLastError();
 }
 
-template <class L, typename T>
+template <class L, typename T, typename S>
 cudaError_t run(int op, const KArgs<T>& a)
 {
     const int K = a.p.ncomp;
     const bool mrt = a.p.collision == COLL_MRT;
     if (K == 1) {
-        if (mrt) return a.geom ? run_k<L, T, 1, COLL_MRT, true>(op, a) : run_k<L, T, 1, COLL_MRT, false>(op, a);
-        return a.geom ? run_k<L, T, 1, COLL_BGK, true>(op, a) : run_k<L, T, 1, COLL_BGK, false>(op, a);
+        if (mrt)
+            return a.geom ? run_k<L, T, S, 1, COLL_MRT, true>(op, a) : run_k<L, T, S, 1, COLL_MRT, false>(op, a);
+        return a.geom ? run_k<L, T, S, 1, COLL_BGK, true>(op, a) : run_k<L, T, S, 1, COLL_BGK, false>(op, a);
     }
-    if (mrt) return a.geom ? run_k<L, T, 2, COLL_MRT, true>(op, a) : run_k<L, T, 2, COLL_MRT, false>(op, a);
-    return a.geom ? run_k<L, T, 2, COLL_BGK, true>(op, a) : run_k<L, T, 2, COLL_BGK, false>(op, a);
+    if (mrt) return a.geom ? run_k<L, T, S, 2, COLL_MRT, true>(op, a) : run_k<L, T, S, 2, COLL_MRT, false>(op, a);
+    return a.geom ? run_k<L, T, S, 2, COLL_BGK, true>(op, a) : run_k<L, T, S, 2, COLL_BGK, false>(op, a);
 }
 
 }  // namespace lbm

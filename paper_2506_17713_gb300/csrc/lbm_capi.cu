@@ -2,11 +2,13 @@
 // geometry set-up, and the launch sequence of one time step.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "args.h"
@@ -19,7 +21,10 @@ struct lbm_ctx {
     lbm_params prm;
     int Q, D;
     long long N;
-    size_t elt;             // bytes per stored value
+    size_t elt;             // bytes per compute value (8 for FP64, 4 otherwise)
+    int pop_kind;           // population storage: 0 = compute type, 1 = FP16, 2 = BF16 (shifted)
+    size_t pop_es;          // bytes per stored population
+    void* stage;            // host-transfer staging (16-bit storage), else null: the idle buffer
     char* ws;
     size_t ws_bytes;
     void* fbuf[2];          // population buffers, [K][Q][N]
@@ -143,7 +148,7 @@ double eos_alpha(int eos, double omega, double Tr)
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t f, psi, rho, solid, bsolid, uprev, status, partials, totals, total;
+    size_t f, psi, rho, solid, bsolid, uprev, stage, status, partials, totals, total;
 };
 
 bool fin(double v) { return std::isfinite(v); }
@@ -156,7 +161,11 @@ lbm_status validate(const lbm_params* p)
     if ((long long)p->nx * p->ny * p->nz >= (1LL << 31)) return LBM_ERR_INVALID_ARG;  // node index in int32
     if (p->lattice == LBM_D2Q9 && p->nz != 1) return LBM_ERR_INVALID_ARG;
     if (p->ncomp != 1 && p->ncomp != 2) return LBM_ERR_INVALID_ARG;
-    if (p->real != LBM_FP32 && p->real != LBM_FP64) return LBM_ERR_INVALID_ARG;
+    if (p->real != LBM_FP32 && p->real != LBM_FP64 && p->real != LBM_FP16S && p->real != LBM_BF16S)
+        return LBM_ERR_INVALID_ARG;
+    if (p->real == LBM_FP16S || p->real == LBM_BF16S)
+        for (int k = 0; k < p->ncomp; ++k)
+            if (!fin(p->rho_ref[k])) return LBM_ERR_INVALID_ARG;
     if (p->collision != LBM_BGK && p->collision != LBM_MRT) return LBM_ERR_INVALID_ARG;
     if (p->velocity != LBM_UEQ_COMPONENT && p->velocity != LBM_UEQ_COMMON) return LBM_ERR_INVALID_ARG;
     const int nf = p->lattice == LBM_D2Q9 ? 4 : 6;
@@ -205,16 +214,21 @@ Layout layout_of(const lbm_params* p)
     const int Q = p->lattice == LBM_D2Q9 ? 9 : 19;
     const int D = p->lattice == LBM_D2Q9 ? 2 : 3;
     const size_t N = (size_t)p->nx * p->ny * p->nz;
-    const size_t e = p->real == LBM_FP64 ? 8 : 4;
+    const size_t e = p->real == LBM_FP64 ? 8 : 4;                       // compute
+    const bool half = p->real == LBM_FP16S || p->real == LBM_BF16S;
+    const size_t es = half ? 2 : e;                                       // stored population
     const size_t K = (size_t)p->ncomp;
     Layout L;
     size_t off = 0;
-    L.f = off;        off += 2 * align256(K * Q * N * e);
+    L.f = off;        off += 2 * align256(K * Q * N * es);
     L.psi = off;      off += align256(K * N * e);
     L.rho = off;      off += align256(K * N * e);
     L.solid = off;    off += align256(N);
     L.bsolid = off;   off += align256(N * sizeof(int));
     L.uprev = off;    off += align256((size_t)D * N * e);
+    // host transfers stage in the idle population buffer; 16-bit buffers are too small
+    // for (1 + D) N doubles (fields in) or Q N floats (populations in and out)
+    L.stage = off;    off += half ? align256(std::max((size_t)(1 + D) * N * 8, (size_t)Q * N * 4)) : 0;
     L.status = off;   off += 256;
     L.partials = off; off += align256(sizeof(double) * 8 * DIAG_BLOCKS);
     L.totals = off;   off += 256;
@@ -303,6 +317,7 @@ void fill_params(const lbm_ctx* c, Params<T>& P)
         P.rho_max[k] = (T)p->rho_max[kk];
         for (int d = 0; d < 3; ++d) P.accel[k][d] = (T)((d2 && d == 2) ? 0.0 : p->body_accel[kk][d]);
         for (int s = 0; s < 2; ++s) P.bc_rho[s][k] = (T)p->bc_rho[s][kk];
+        P.rho_ref[k] = (p->real == LBM_FP16S || p->real == LBM_BF16S) ? (T)p->rho_ref[kk] : T(0);
     }
 }
 
@@ -312,8 +327,8 @@ KArgs<T> base_args(lbm_ctx* c, const Params<T>& P)
     KArgs<T> a;
     std::memset(&a, 0, sizeof(a));
     a.p = P;
-    a.f_src = (const T*)c->fbuf[c->cur];
-    a.f_dst = (T*)c->fbuf[c->cur ^ 1];
+    a.f_src = c->fbuf[c->cur];
+    a.f_dst = c->fbuf[c->cur ^ 1];
     a.psi = (T*)c->psi;
     a.rho = (T*)c->rho;
     a.solid = c->solid;
@@ -334,7 +349,15 @@ KArgs<T> base_args(lbm_ctx* c, const Params<T>& P)
 template <typename T>
 cudaError_t dispatch(lbm_ctx* c, int op, const KArgs<T>& a)
 {
-    cudaError_t e = c->prm.lattice == LBM_D2Q9 ? run<D2Q9, T>(op, a) : run<D3Q19, T>(op, a);
+    cudaError_t e;
+    if constexpr (std::is_same<T, float>::value) {
+        const bool d2 = c->prm.lattice == LBM_D2Q9;
+        if (c->pop_kind == 1) e = d2 ? run<D2Q9, T, __half>(op, a) : run<D3Q19, T, __half>(op, a);
+        else if (c->pop_kind == 2) e = d2 ? run<D2Q9, T, __nv_bfloat16>(op, a) : run<D3Q19, T, __nv_bfloat16>(op, a);
+        else e = d2 ? run<D2Q9, T, T>(op, a) : run<D3Q19, T, T>(op, a);
+    } else {
+        e = c->prm.lattice == LBM_D2Q9 ? run<D2Q9, T, T>(op, a) : run<D3Q19, T, T>(op, a);
+    }
     if (e == cudaSuccess) {
         if (op == OP_DIAG) c->launches += 2;
         else if (op != OP_VIRTUAL || c->n_bsolid > 0) c->launches += 1;
@@ -469,7 +492,7 @@ int build_boundary_list(const lbm_ctx* c, const uint8_t* solid, std::vector<int>
 }
 
 // The second population buffer doubles as staging space for host transfers.
-void* staging(lbm_ctx* c) { return c->fbuf[c->cur ^ 1]; }
+void* staging(lbm_ctx* c) { return c->stage ? c->stage : c->fbuf[c->cur ^ 1]; }
 
 }  // namespace
 
@@ -503,9 +526,12 @@ lbm_status lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void
     c->D = p->lattice == LBM_D2Q9 ? 2 : 3;
     c->N = (long long)p->nx * p->ny * p->nz;
     c->elt = p->real == LBM_FP64 ? 8 : 4;
+    c->pop_kind = p->real == LBM_FP16S ? 1 : (p->real == LBM_BF16S ? 2 : 0);
+    c->pop_es = c->pop_kind ? 2 : c->elt;
     c->ws = (char*)d_workspace;
     c->ws_bytes = bytes;
-    const size_t fbytes = align256((size_t)p->ncomp * c->Q * c->N * c->elt);
+    const size_t fbytes = align256((size_t)p->ncomp * c->Q * c->N * c->pop_es);
+    c->stage = c->pop_kind ? c->ws + L.stage : nullptr;
     c->fbuf[0] = c->ws + L.f;
     c->fbuf[1] = c->ws + L.f + fbytes;
     c->cur = 0;
@@ -614,7 +640,7 @@ lbm_status init_fields_t(lbm_ctx* c, int comp, const double* rho, const double* 
         if (e != cudaSuccess) return fail_cuda(c, e);
     }
     KArgs<T> a = base_args<T>(c, P);
-    a.f_dst = (T*)c->fbuf[c->cur];
+    a.f_dst = c->fbuf[c->cur];
     a.comp = comp;
     a.in_rho = drho;
     a.in_u = du;
@@ -752,7 +778,7 @@ lbm_status set_pops_t(lbm_ctx* c, int comp, const void* f, int where, const Para
 {
     KArgs<T> a = base_args<T>(c, P);
     a.comp = comp;
-    a.f_dst = (T*)c->fbuf[c->cur];
+    a.f_dst = c->fbuf[c->cur];
     const T* src = (const T*)f;
     cudaError_t e = cudaSuccess;
     if (where == LBM_HOST) {

@@ -17,7 +17,7 @@ LBM_OK = 0
 STATUS = {0: "LBM_OK", 1: "LBM_ERR_INVALID_ARG", 2: "LBM_ERR_WORKSPACE", 3: "LBM_ERR_CUDA",
           4: "LBM_ERR_UNSTABLE", 5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE"}
 LBM_D2Q9, LBM_D3Q19 = 0, 1
-LBM_FP32, LBM_FP64 = 0, 1
+LBM_FP32, LBM_FP64, LBM_FP16S, LBM_BF16S = 0, 1, 2, 3
 LBM_BGK, LBM_MRT = 0, 1
 LBM_UEQ_COMPONENT, LBM_UEQ_COMMON = 0, 1
 PSI = {"eos": 0, "rho": 1, "exp": 2}
@@ -52,6 +52,7 @@ class lbm_params(C.Structure):
         ("body_accel", (C.c_double * 3) * 2),
         ("bc", C.c_int * 6), ("bc_rho", (C.c_double * 2) * 6),
         ("schedule", C.c_int),
+        ("rho_ref", C.c_double * 2),
     ]
 
 
@@ -220,7 +221,10 @@ def params_from_case(case):
     p.lattice = LBM_D2Q9 if case["lattice"] == "D2Q9" else LBM_D3Q19
     p.nx, p.ny, p.nz = [int(v) for v in case["shape"]]
     p.ncomp = int(case.get("ncomp", 1))
-    p.real = LBM_FP64 if case.get("real", "f32") == "f64" else LBM_FP32
+    p.real = {"f32": LBM_FP32, "f64": LBM_FP64, "f16s": LBM_FP16S, "bf16s": LBM_BF16S}[case.get("real", "f32")]
+    rr = case.get("rho_ref", [1.0, 1.0])
+    for k in range(2):
+        p.rho_ref[k] = float(rr[k] if k < len(rr) else rr[0])
     p.collision = LBM_MRT if case.get("collision", "BGK") == "MRT" else LBM_BGK
     p.velocity = LBM_UEQ_COMMON if case.get("velocity", "component") == "common" else LBM_UEQ_COMPONENT
     p.tau[:] = _two(case.get("tau"), 1.0)

@@ -56,6 +56,12 @@ def test_workspace_size_layout(lib):
     assert n64 > n
     n2 = lbm.lbm_workspace_size(lbm.params_from_case(dict(c, ncomp=2)))
     assert n2 >= n + 2 * 19 * N * 4
+    # 16-bit population storage: 2-byte populations plus a staging region for host
+    # transfers (Q N floats here)
+    for real in ("f16s", "bf16s"):
+        nh = lbm.lbm_workspace_size(lbm.params_from_case(dict(c, real=real)))
+        assert nh >= 2 * 19 * N * 2 + 2 * N * 4 + N + 4 * N + 3 * N * 4 + 19 * N * 4
+        assert nh < n + 19 * N * 4
 
 
 @pytest.mark.parametrize("bad", [
@@ -70,6 +76,7 @@ def test_workspace_size_layout(lib):
     dict(mrt_rates=[[2.5] * 19]),
     dict(T_red=[0.0, 0.0]),
     dict(shape=(2048, 1024, 1024)),            # 2^31 nodes: node indices are 32-bit
+    dict(real="f16s", rho_ref=[float("nan"), 1.0]),
 ])
 def test_rejects_invalid_parameters(lib, bad):
     from paper_2506_17713_gb300 import lbm
@@ -101,3 +108,14 @@ def test_params_mapping_roundtrip():
     assert p.psi_kind[0] == lbm.PSI["rho"] and p.bc[0] == lbm.BC["pressure"]
     assert abs(p.g[0][1] - c["g"][0][1]) < 1e-15
     assert abs(p.bc_rho[0][1] - c["bc_rho"][0][1]) < 1e-15
+    p16 = lbm.params_from_case(dict(c, real="bf16s", rho_ref=[0.25, 2.0]))
+    assert p16.real == lbm.LBM_BF16S and list(p16.rho_ref) == [0.25, 2.0]
+
+
+def test_mass_noalloc_rejects_16bit_storage_before_any_device_call(lib):
+    # validation happens on the host: the (never dereferenced) device pointer is a dummy
+    from paper_2506_17713_gb300 import lbm
+    for real in ("f16s", "bf16s"):
+        p = lbm.params_from_case(_case(real=real))
+        mass = (C.c_double * 2)()
+        assert lib.lbm_mass_noalloc(C.byref(p), C.c_void_p(256), mass, None) == 1
