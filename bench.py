@@ -31,6 +31,8 @@ WORKLOADS = {
     "exp256": "D3Q19 Shan-Chen psi=exp(-1/rho) BGK 256^3 FP32, droplet R=30",
     "porous400": "D3Q19 two-component Shan-Chen 400^3 FP32, GRF porous medium (porosity 0.15, "
                  "corr. length 6, seed 7), wetting, constant-density x faces",
+    "batch64": "64 D3Q19 sphere-pack drainage samples, box edges U[64,192] (seed 2024), overlapping spheres "
+               "r U[8,12] to porosity 0.38, PR T=0.8Tc MRT FP32, wetting solids, per-sample inlet pressure step",
 }
 
 
@@ -58,6 +60,8 @@ def make_case(name, n=256):
                                               width=max(2.0, cases.PR06_WIDTH * f))
     elif name == "exp256":
         case, init = cases.droplet_3d_exp(n=n, radius=30.0 * n / 256)
+    elif name == "batch64":   # the oracle-timed stand-in: the first sample of the batch
+        case, init = cases.sphere_pack_batch(count=1)[0]
     elif name == "porous400":
         m = 400 if n == 256 else n
         case, init = cases.porous_two_component(shape=(m, m, m))
@@ -272,6 +276,103 @@ def run_reference(args):
 # Our arm
 # ---------------------------------------------------------------------------
 
+def run_batch(args):
+    """Many lattices in one batch (one persistent launch per pass, two steps per CUDA
+    graph replay), against the same lattices stepped one after another."""
+    import torch
+    from paper_2506_17713_gb300 import Batch, Lattice
+    from synth import cases
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    count = args.batch_count
+    samples = cases.sphere_pack_batch(count=count, edge_lo=args.batch_edge_lo, edge_hi=args.batch_edge_hi)
+    lats = []
+    for case, init in samples:
+        case["real"] = args.real
+        if args.real in ("f16s", "bf16s"):
+            case["rho_ref"] = [case["bc_rho"][1][0]] * 2
+        lat = Lattice(case)
+        lat.set_geometry(init["solid"])
+        lat.init_fields(0, init["rho"][0])
+        lats.append(lat)
+    N = sum(l.N for l in lats)
+    n_fluid = sum(int(np.count_nonzero(init["solid"] == 0)) for _, init in samples)
+    stream = lats[0].stream
+    batch = Batch(lats)
+    cfg = batch.autotune()
+    batch.step(args.warmup + (args.warmup & 1))
+    torch.cuda.synchronize()
+
+    def timed(fn, steps):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        barrier(world, dev)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        fn(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / 1e3
+
+    steps = args.steps + (args.steps & 1)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    n0 = batch.launches()
+    t_batch = timed(batch.step, steps)
+    launches = batch.launches() - n0
+    clk = clocks.stop()
+
+    def sequential(k):
+        for _ in range(k):
+            for lat in lats:
+                lat.step(1)
+    seq_steps = max(2, min(steps, args.batch_seq_steps))
+    t_seq = timed(sequential, seq_steps)
+    t_max = reduce_max(t_batch, world, dev)
+    mlups = aggregate(N * steps, t_max, world) / 1e6
+    seq_mlups = N * seq_steps / t_seq / 1e6
+    # bytes per fluid node of one step: density (K Q + psi + rho + mask + list) and collide
+    ab = algorithmic_bytes(samples[0][0] | {"real": args.real}, fluid_list=True)
+    step_gbs = ab["step"] * n_fluid * steps / t_batch / 1e9
+    peak, peak_kind = load_peaks()
+    if rank != 0:
+        barrier(world, dev)
+        return
+    line = {
+        "metric": "D3Q19 Shan-Chen MLUPS", "value": round(mlups, 1), "unit": "MLUPS",
+        "n_gpus": world, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * t_max / steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS["batch64"].replace("64 D3Q19", "%d D3Q19" % count)
+                   .replace("U[64,192]", "U[%d,%d]" % (args.batch_edge_lo, args.batch_edge_hi)),
+                   "lattices": count, "nodes": N, "fluid_nodes": n_fluid,
+                   "mflups": round(mlups * n_fluid / N, 1), "storage": STORAGE[args.real],
+                   "launch": "one persistent launch per pass for all lattices, 2 steps per CUDA graph replay",
+                   "autotuned": {"density": cfg[0], "virtual": cfg[1], "collide": cfg[2]},
+                   "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "inputs larger than L2 (%.1f GB of populations)" % (
+                       2 * 19 * N * (2 if args.real in ("f16s", "bf16s") else 4) / 1e9)},
+        "roofline": {"bound": "hbm", "kernel": "batched step (density + virtual + collide passes)",
+                     "achieved": round(step_gbs, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(step_gbs / peak, 4), "peak_kind": peak_kind, "traffic": None,
+                     "bytes_per_lu": ab["step"], "units_per_launch": n_fluid},
+        "sequential": {"value": round(seq_mlups, 1), "unit": "MLUPS", "steps": seq_steps,
+                       "ms_per_step": round(1e3 * t_seq / seq_steps, 4),
+                       "launch": "lbm_step per lattice, one lattice after another"},
+        "speedup_vs_sequential": round(mlups / seq_mlups, 3),
+        "cpu_baseline": None, "e2e": None,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        barrier(world, dev)
+    batch.close()
+
+
 def run_ours(args):
     import torch
     from paper_2506_17713_gb300 import Lattice, lbm
@@ -429,11 +530,18 @@ def main():
                     help="CPU time of the oracle sample behind cpu_baseline")
     ap.add_argument("--ref-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--batch-edge-lo", type=int, default=64)
+    ap.add_argument("--batch-edge-hi", type=int, default=192)
+    ap.add_argument("--batch-seq-steps", type=int, default=50,
+                    help="steps of the sequential comparison (batch64)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch64":
+        run_batch(args)
     else:
         run_ours(args)
 

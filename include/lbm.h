@@ -210,6 +210,45 @@ void lbm_destroy(lbm_ctx* ctx);
 const char* lbm_status_str(lbm_status s);
 
 /*
+ * Batches (the paper advances many porous samples, Section 3.4; its code does
+ * not batch them). A batch advances several lattices in lock step with one
+ * persistent kernel launch per pass (density, virtual density, collide) for all of
+ * them, two time steps per replay of a CUDA graph captured on the first call.
+ * The lattices of a batch may differ in size and geometry, but must share
+ * lattice, real, ncomp, collision and whether they have solids or closed faces.
+ * Every context must outlive the batch, and the caller orders work on the
+ * contexts' streams and the batch stream (e.g. by using one stream for all).
+ * Results are those of lbm_step on each lattice, bit for bit.
+ *
+ * lbm_batch_workspace_size: device bytes of the batch's lattice table for ctxs[0..n).
+ *   LBM_ERR_INVALID_ARG if n < 1, a context is NULL or the contexts differ in the
+ *   properties above.
+ * lbm_batch_create: d_workspace (device, 256-byte aligned, >= that many bytes, owned
+ *   by the caller), stream = the stream every batch step is enqueued on. Each context
+ *   may appear once. The batch itself allocates no device memory; the CUDA graph it
+ *   instantiates holds driver resources until lbm_batch_destroy.
+ * lbm_batch_autotune: times each pass over the current state for CTA sizes 128 and
+ *   256 and persistent grids of 2 to 16 CTAs (of 256 threads) per SM, and keeps the
+ *   fastest. The passes it repeats are idempotent, so the state does not change
+ *   (only the status counters of a lattice whose density is already out of range
+ *   count again). config (may be NULL): [3][2] int, the chosen (CTA size, grid) of
+ *   the density, virtual-density and collide passes. Synchronises the batch stream.
+ * lbm_batch_step: nsteps time steps of every lattice, enqueued on the batch stream.
+ *   Returns the sticky error of any lattice (LBM_ERR_STATE before its fields are
+ *   initialised); a CUDA failure makes every lattice of the batch sticky.
+ * lbm_batch_launches: kernel launches issued by batch steps so far (graph replays
+ *   count their kernels); per-context launch counters do not include them.
+ */
+typedef struct lbm_batch lbm_batch;
+lbm_status lbm_batch_workspace_size(lbm_ctx* const* ctxs, int n, size_t* bytes);
+lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, void* d_workspace, size_t bytes, void* stream,
+                            lbm_batch** out);
+lbm_status lbm_batch_autotune(lbm_batch* b, int* config);
+lbm_status lbm_batch_step(lbm_batch* b, int nsteps);
+long long lbm_batch_launches(const lbm_batch* b);
+void lbm_batch_destroy(lbm_batch* b);
+
+/*
  * Mass without allocation. The paper has no counterpart: this is a service for callers
  * that cannot allocate device memory at all -- code running while a CUDA graph is being
  * captured, processes where a framework owns every allocation, or callers whose memory

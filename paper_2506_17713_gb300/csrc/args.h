@@ -119,6 +119,23 @@ struct KArgs {
     cudaStream_t stream;
 };
 
+// One lattice of a batch (lbm_batch_*): its kernel arguments for both buffer
+// parities (a[0] pulls from the buffer that holds the current populations) and,
+// per batched pass, the first virtual CTA of this lattice in the batch's CTA space.
+enum : int { BOP_DENSITY = 0, BOP_VIRTUAL = 1, BOP_COLLIDE = 2 };
+
+template <typename T>
+struct BatchItem {
+    KArgs<T> a[2];
+    long long vb0[3];    // first virtual CTA per pass (density, virtual, collide)
+};
+
+// launch shape of one batched pass: CTA size, persistent grid, virtual CTAs in all
+struct BatchLaunch {
+    int block, grid;
+    long long nvb;
+};
+
 constexpr int DIAG_BLOCKS = 1024;
 constexpr int DIAG_THREADS = 256;
 
@@ -126,5 +143,11 @@ constexpr int DIAG_THREADS = 256;
 // holding shifted values for T = float)
 template <class L, typename T, typename S>
 cudaError_t run(int op, const KArgs<T>& a);
+
+// One batched pass (BOP_*) over every lattice of the table in one persistent launch.
+// The lattices share lattice, types, K, collision and the geometry flag of `shape`.
+template <class L, typename T, typename S>
+cudaError_t run_batch(int bop, const KArgs<T>& shape, const BatchItem<T>* items, int n_items,
+                      const BatchLaunch& launch, int parity, cudaStream_t stream);
 
 }  // namespace lbm

@@ -4,4 +4,7 @@
 
 namespace lbm {
 template cudaError_t run<D2Q9, float, __nv_bfloat16>(int op, const KArgs<float>& a);
+template cudaError_t run_batch<D2Q9, float, __nv_bfloat16>(int bop, const KArgs<float>& shape, const BatchItem<float>* items,
+                                              int n_items, const BatchLaunch& launch, int parity,
+                                              cudaStream_t stream);
 }  // namespace lbm

@@ -4,4 +4,7 @@
 
 namespace lbm {
 template cudaError_t run<D2Q9, double, double>(int op, const KArgs<double>& a);
+template cudaError_t run_batch<D2Q9, double, double>(int bop, const KArgs<double>& shape, const BatchItem<double>* items,
+                                              int n_items, const BatchLaunch& launch, int parity,
+                                              cudaStream_t stream);
 }  // namespace lbm

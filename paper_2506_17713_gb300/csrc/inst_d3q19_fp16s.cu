@@ -4,4 +4,7 @@
 
 namespace lbm {
 template cudaError_t run<D3Q19, float, __half>(int op, const KArgs<float>& a);
+template cudaError_t run_batch<D3Q19, float, __half>(int bop, const KArgs<float>& shape, const BatchItem<float>* items,
+                                              int n_items, const BatchLaunch& launch, int parity,
+                                              cudaStream_t stream);
 }  // namespace lbm

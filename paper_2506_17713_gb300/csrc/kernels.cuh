@@ -1055,10 +1055,8 @@ LBM_HD bool bad_density(T r)
 }
 
 template <class L, typename T, typename S, int K, bool GEOM>
-__global__ void __launch_bounds__(256, K == 1 ? 0 : 5) k_density(const KArgs<T> a)
+__device__ __forceinline__ void density_node(const KArgs<T>& a, const Node& nd)
 {
-    Node nd;
-    if (!fluid_node<GEOM>(a, nd)) return;
     const long long N = a.p.N;
     bool bad = false, clamp = false;
     T f[K][L::Q];
@@ -1076,11 +1074,17 @@ __global__ void __launch_bounds__(256, K == 1 ? 0 : 5) k_density(const KArgs<T> 
     if (clamp) atomicAdd(a.status + ST_PSI_CLAMP, 1);
 }
 
-template <class L, typename T, int K>
-__global__ void __launch_bounds__(256) k_virtual(const KArgs<T> a)
+template <class L, typename T, typename S, int K, bool GEOM>
+__global__ void __launch_bounds__(256, K == 1 ? 0 : 5) k_density(const KArgs<T> a)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.n_bsolid) return;
+    Node nd;
+    if (fluid_node<GEOM>(a, nd)) density_node<L, T, S, K, GEOM>(a, nd);
+}
+
+// virtual density and psi at boundary solid t (Eq. improved_virtual_density)
+template <class L, typename T, int K>
+__device__ __forceinline__ void virtual_node(const KArgs<T>& a, int t)
+{
     const Params<T>& P = a.p;
     const long long s = a.bsolid[t];
     const int x = (int)(s % P.nx), y = (int)((s / P.nx) % P.ny), z = (int)(s / ((long long)P.nx * P.ny));
@@ -1105,11 +1109,16 @@ __global__ void __launch_bounds__(256) k_virtual(const KArgs<T> a)
     }
 }
 
-template <class L, typename T, typename S, int K, int COLL, bool GEOM>
-__global__ void __launch_bounds__(256, K == 1 ? 4 : 3) k_collide(const KArgs<T> a)
+template <class L, typename T, int K>
+__global__ void __launch_bounds__(256) k_virtual(const KArgs<T> a)
 {
-    Node nd;
-    if (!fluid_node<GEOM>(a, nd)) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < a.n_bsolid) virtual_node<L, T, K>(a, t);
+}
+
+template <class L, typename T, typename S, int K, int COLL, bool GEOM>
+__device__ __forceinline__ void collide_node(const KArgs<T>& a, const Node& nd)
+{
     const Params<T>& P = a.p;
     const long long N = P.N;
     T f[K][L::Q];
@@ -1156,6 +1165,13 @@ __global__ void __launch_bounds__(256, K == 1 ? 4 : 3) k_collide(const KArgs<T> 
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) store_pop<L, T, S>(dst, (long long)i * N, i, f[k][i], P.rho_ref[k]);
     }
+}
+
+template <class L, typename T, typename S, int K, int COLL, bool GEOM>
+__global__ void __launch_bounds__(256, K == 1 ? 4 : 3) k_collide(const KArgs<T> a)
+{
+    Node nd;
+    if (fluid_node<GEOM>(a, nd)) collide_node<L, T, S, K, COLL, GEOM>(a, nd);
 }
 
 // ---------------------------------------------------------------------------
@@ -1467,6 +1483,108 @@ static __global__ void k_diag_final(const double* __restrict__ partials, double*
 }
 
 // ---------------------------------------------------------------------------
+// Batched passes: many lattices in one persistent launch
+// ---------------------------------------------------------------------------
+//
+// The CTAs of every lattice of a batch form one virtual CTA space (each lattice
+// needs ceil(units / blockDim) of them: fluid nodes for density / collide,
+// boundary solids for the virtual pass). A persistent grid walks that space; a
+// CTA finds the lattice of its virtual CTA by binary search over the first
+// virtual CTA of each lattice, stages that lattice's kernel arguments in shared
+// memory, and runs the same per-node code as the single-lattice kernels.
+
+template <typename T>
+__device__ __forceinline__ int batch_item_of(const BatchItem<T>* __restrict__ items, int n, int bop, long long vb)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid].vb0[bop] <= vb) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// copy the kernel arguments of one lattice into shared memory (whole CTA)
+template <typename T>
+__device__ __forceinline__ void stage_args(KArgs<T>& dst, const KArgs<T>& src)
+{
+    static_assert(sizeof(KArgs<T>) % sizeof(int) == 0, "KArgs is copied in words");
+    const int* s = reinterpret_cast<const int*>(&src);
+    int* d = reinterpret_cast<int*>(&dst);
+    for (int w = threadIdx.x; w < (int)(sizeof(KArgs<T>) / sizeof(int)); w += blockDim.x) d[w] = s[w];
+}
+
+// node of unit t of a lattice: the t-th fluid node (fluid list) or node t
+template <typename T>
+__device__ __forceinline__ bool node_of_unit(const KArgs<T>& a, long long t, Node& nd)
+{
+    uint32_t n;
+    if (a.fluid) {
+        if (t >= a.n_fluid) return false;
+        n = (uint32_t)a.fluid[t];
+    } else {
+        if (t >= a.p.N) return false;
+        n = (uint32_t)t;
+    }
+    const uint32_t yz = fast_div(n, a.p.div_nx);
+    const uint32_t z = fast_div(yz, a.p.div_ny);
+    nd.x = (int)(n - yz * (uint32_t)a.p.nx);
+    nd.y = (int)(yz - z * (uint32_t)a.p.ny);
+    nd.z = (int)z;
+    nd.n = (long long)n;
+    return true;
+}
+
+template <class L, typename T, typename S, int K, int COLL, bool GEOM, int BOP>
+__global__ void __launch_bounds__(256, BOP == BOP_COLLIDE ? (K == 1 ? 4 : 3) : (K == 1 ? 0 : 5))
+kb_pass(const BatchItem<T>* __restrict__ items, int n_items, long long nvb, int parity)
+{
+    __shared__ __align__(16) unsigned char sbuf[sizeof(KArgs<T>)];
+    KArgs<T>& sa = *reinterpret_cast<KArgs<T>*>(sbuf);
+    int staged = -1;
+    for (long long vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+        const int s = batch_item_of(items, n_items, BOP, vb);
+        if (s != staged) {   // the same for the whole CTA
+            __syncthreads();
+            stage_args(sa, items[s].a[parity]);
+            __syncthreads();
+            staged = s;
+        }
+        const long long t = (vb - items[s].vb0[BOP]) * blockDim.x + threadIdx.x;
+        if constexpr (BOP == BOP_VIRTUAL) {
+            if (t < sa.n_bsolid) virtual_node<L, T, K>(sa, (int)t);
+        } else {
+            Node nd;
+            if (node_of_unit(sa, t, nd)) {
+                if constexpr (BOP == BOP_DENSITY) density_node<L, T, S, K, GEOM>(sa, nd);
+                else collide_node<L, T, S, K, COLL, GEOM>(sa, nd);
+            }
+        }
+    }
+}
+
+template <class L, typename T, typename S, int K, int COLL, bool GEOM>
+cudaError_t run_batch_k(int bop, const BatchItem<T>* items, int n_items, const BatchLaunch& b, int parity,
+                        cudaStream_t st)
+{
+    if (b.nvb <= 0) return cudaSuccess;
+    switch (bop) {
+    case BOP_DENSITY:
+        kb_pass<L, T, S, K, COLL, GEOM, BOP_DENSITY><<<b.grid, b.block, 0, st>>>(items, n_items, b.nvb, parity);
+        break;
+    case BOP_VIRTUAL:
+        kb_pass<L, T, S, K, COLL, GEOM, BOP_VIRTUAL><<<b.grid, b.block, 0, st>>>(items, n_items, b.nvb, parity);
+        break;
+    case BOP_COLLIDE:
+        kb_pass<L, T, S, K, COLL, GEOM, BOP_COLLIDE><<<b.grid, b.block, 0, st>>>(items, n_items, b.nvb, parity);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 
@@ -1525,6 +1643,22 @@ cudaError_t run(int op, const KArgs<T>& a)
     }
     if (mrt) return a.geom ? run_k<L, T, S, 2, COLL_MRT, true>(op, a) : run_k<L, T, S, 2, COLL_MRT, false>(op, a);
     return a.geom ? run_k<L, T, S, 2, COLL_BGK, true>(op, a) : run_k<L, T, S, 2, COLL_BGK, false>(op, a);
+}
+
+template <class L, typename T, typename S>
+cudaError_t run_batch(int bop, const KArgs<T>& shape, const BatchItem<T>* items, int n_items,
+                      const BatchLaunch& launch, int parity, cudaStream_t st)
+{
+    const int K = shape.p.ncomp;
+    const bool mrt = shape.p.collision == COLL_MRT, geom = shape.geom != 0;
+#define LBM_RB(KK, CC, GG) run_batch_k<L, T, S, KK, CC, GG>(bop, items, n_items, launch, parity, st)
+    if (K == 1) {
+        if (mrt) return geom ? LBM_RB(1, COLL_MRT, true) : LBM_RB(1, COLL_MRT, false);
+        return geom ? LBM_RB(1, COLL_BGK, true) : LBM_RB(1, COLL_BGK, false);
+    }
+    if (mrt) return geom ? LBM_RB(2, COLL_MRT, true) : LBM_RB(2, COLL_MRT, false);
+    return geom ? LBM_RB(2, COLL_BGK, true) : LBM_RB(2, COLL_BGK, false);
+#undef LBM_RB
 }
 
 }  // namespace lbm

@@ -919,6 +919,325 @@ void lbm_destroy(lbm_ctx* c)
     delete c;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches: many lattices advanced by one persistent launch per pass, two steps
+// per CUDA graph replay
+// ---------------------------------------------------------------------------
+
+struct lbm_batch {
+    std::vector<lbm_ctx*> ctx;
+    cudaStream_t stream;      // the caller's stream: uploads, graph replays, direct passes
+    cudaStream_t capture;     // private stream the graph is captured on (the legacy default
+                              // stream cannot be captured)
+    cudaStream_t launch_on;   // where batch_pass enqueues (stream, or capture while capturing)
+    char* ws;
+    size_t ws_bytes;
+    BatchLaunch launch[3];
+    std::vector<unsigned char> host;   // item table as last uploaded
+    cudaGraphExec_t exec;
+    bool graph_ok;
+    long long launches;
+    int sms;
+};
+
+namespace {
+
+size_t batch_item_bytes(const lbm_ctx* c)
+{
+    return c->elt == 8 ? sizeof(BatchItem<double>) : sizeof(BatchItem<float>);
+}
+
+// lattices of one batch share every template parameter of the batched kernels
+bool batch_compatible(const lbm_ctx* a, const lbm_ctx* b)
+{
+    return a->prm.lattice == b->prm.lattice && a->prm.real == b->prm.real && a->prm.ncomp == b->prm.ncomp &&
+           a->prm.collision == b->prm.collision && (a->geom != 0) == (b->geom != 0);
+}
+
+long long batch_units(const lbm_ctx* c, int bop)
+{
+    if (bop == BOP_VIRTUAL) return c->n_bsolid;
+    return c->any_solid ? c->n_fluid : c->N;
+}
+
+template <typename T>
+const Params<T>& params_of(const lbm_ctx* c);
+template <>
+const Params<float>& params_of<float>(const lbm_ctx* c) { return c->pf; }
+template <>
+const Params<double>& params_of<double>(const lbm_ctx* c) { return c->pd; }
+
+// item table for the current buffers of every lattice and the current CTA sizes
+template <typename T>
+void batch_table(lbm_batch* b)
+{
+    const int n = (int)b->ctx.size();
+    std::vector<BatchItem<T>> items((size_t)n);
+    long long vb[3] = {0, 0, 0};
+    for (int i = 0; i < n; ++i) {
+        lbm_ctx* c = b->ctx[(size_t)i];
+        BatchItem<T>& it = items[(size_t)i];
+        std::memset(&it, 0, sizeof(it));
+        it.a[0] = base_args<T>(c, params_of<T>(c));
+        it.a[1] = it.a[0];
+        it.a[1].f_src = it.a[0].f_dst;
+        it.a[1].f_dst = const_cast<void*>(it.a[0].f_src);
+        for (int op = 0; op < 3; ++op) {
+            it.vb0[op] = vb[op];
+            const long long blk = b->launch[op].block;
+            vb[op] += (batch_units(c, op) + blk - 1) / blk;
+        }
+    }
+    for (int op = 0; op < 3; ++op) b->launch[op].nvb = vb[op];
+    b->host.assign(reinterpret_cast<unsigned char*>(items.data()),
+                   reinterpret_cast<unsigned char*>(items.data()) + sizeof(BatchItem<T>) * (size_t)n);
+}
+
+void batch_grid(lbm_batch* b, int op, int ctas_per_sm)
+{
+    BatchLaunch& l = b->launch[op];
+    const long long want = (long long)b->sms * ctas_per_sm;
+    l.grid = (int)std::max(1LL, std::min(want, std::max(l.nvb, 1LL)));
+}
+
+cudaError_t batch_upload(lbm_batch* b)
+{
+    return cudaMemcpyAsync(b->ws, b->host.data(), b->host.size(), cudaMemcpyHostToDevice, b->stream);
+}
+
+template <typename T>
+cudaError_t batch_pass(lbm_batch* b, int op, int parity)
+{
+    const lbm_ctx* c0 = b->ctx[0];
+    const BatchItem<T>* items = reinterpret_cast<const BatchItem<T>*>(b->ws);
+    const BatchItem<T>* h = reinterpret_cast<const BatchItem<T>*>(b->host.data());
+    const KArgs<T>& shape = h[0].a[0];
+    const int n = (int)b->ctx.size();
+    const bool d2 = c0->prm.lattice == LBM_D2Q9;
+    cudaStream_t st = b->launch_on;
+    if constexpr (std::is_same<T, float>::value) {
+        if (c0->pop_kind == 1)
+            return d2 ? run_batch<D2Q9, T, __half>(op, shape, items, n, b->launch[op], parity, st)
+                      : run_batch<D3Q19, T, __half>(op, shape, items, n, b->launch[op], parity, st);
+        if (c0->pop_kind == 2)
+            return d2 ? run_batch<D2Q9, T, __nv_bfloat16>(op, shape, items, n, b->launch[op], parity, st)
+                      : run_batch<D3Q19, T, __nv_bfloat16>(op, shape, items, n, b->launch[op], parity, st);
+    }
+    return d2 ? run_batch<D2Q9, T, T>(op, shape, items, n, b->launch[op], parity, st)
+              : run_batch<D3Q19, T, T>(op, shape, items, n, b->launch[op], parity, st);
+}
+
+// one time step of every lattice: density, virtual density at boundary solids, collide
+template <typename T>
+cudaError_t batch_step(lbm_batch* b, int parity, long long* launches)
+{
+    cudaError_t e = cudaSuccess;
+    for (int op = 0; op < 3 && e == cudaSuccess; ++op) {
+        if (b->launch[op].nvb <= 0) continue;
+        e = batch_pass<T>(b, op, parity);
+        if (e == cudaSuccess && launches) *launches += 1;
+    }
+    return e;
+}
+
+lbm_status batch_fail(lbm_batch* b, cudaError_t e)
+{
+    for (lbm_ctx* c : b->ctx) c->sticky = LBM_ERR_CUDA;
+    (void)e;
+    return LBM_ERR_CUDA;
+}
+
+template <typename T>
+lbm_status batch_step_t(lbm_batch* b, int nsteps)
+{
+    batch_table<T>(b);
+    cudaError_t e = batch_upload(b);
+    if (e != cudaSuccess) return batch_fail(b, e);
+    long long per_pair = 0;
+    for (int op = 0; op < 3; ++op) per_pair += b->launch[op].nvb > 0 ? 2 : 0;
+    if (!b->graph_ok && nsteps >= 2) {
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            b->launch_on = b->capture;
+            cudaError_t e1 = batch_step<T>(b, 0, nullptr);
+            if (e1 == cudaSuccess) e1 = batch_step<T>(b, 1, nullptr);
+            b->launch_on = b->stream;
+            e = cudaStreamEndCapture(b->capture, &g);
+            if (e == cudaSuccess) e = e1;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) return batch_fail(b, e);
+        b->graph_ok = true;
+    }
+    for (int q = 0; q < nsteps / 2 && e == cudaSuccess; ++q) {
+        e = cudaGraphLaunch(b->exec, b->stream);
+        if (e == cudaSuccess) b->launches += per_pair;
+    }
+    if (e == cudaSuccess && (nsteps & 1)) {
+        e = batch_step<T>(b, 0, &b->launches);
+        if (e == cudaSuccess)
+            for (lbm_ctx* c : b->ctx) c->cur ^= 1;
+    }
+    if (e != cudaSuccess) return batch_fail(b, e);
+    return LBM_OK;
+}
+
+// time `reps` launches of one pass with CUDA events (after one untimed launch)
+template <typename T>
+float batch_time_pass(lbm_batch* b, int op, int reps, cudaEvent_t e0, cudaEvent_t e1)
+{
+    batch_table<T>(b);
+    if (batch_upload(b) != cudaSuccess) return -1.0f;
+    if (batch_pass<T>(b, op, 0) != cudaSuccess) return -1.0f;
+    if (cudaEventRecord(e0, b->stream) != cudaSuccess) return -1.0f;
+    for (int r = 0; r < reps; ++r)
+        if (batch_pass<T>(b, op, 0) != cudaSuccess) return -1.0f;
+    if (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return -1.0f;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return -1.0f;
+    return ms / reps;
+}
+
+template <typename T>
+lbm_status batch_autotune_t(lbm_batch* b, int* config)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return batch_fail(b, cudaErrorUnknown);
+    }
+    static const int blocks[2] = {128, 256};
+    static const int per_sm[4] = {2, 4, 8, 16};
+    // density first, so that the collide pass is timed on fresh psi
+    const int order[3] = {BOP_DENSITY, BOP_VIRTUAL, BOP_COLLIDE};
+    lbm_status st = LBM_OK;
+    for (int oi = 0; oi < 3 && st == LBM_OK; ++oi) {
+        const int op = order[oi];
+        float best = -1.0f;
+        int bb = b->launch[op].block, bg = 4;
+        for (int bi = 0; bi < 2 && st == LBM_OK; ++bi)
+            for (int pi = 0; pi < 4; ++pi) {
+                b->launch[op].block = blocks[bi];
+                batch_table<T>(b);
+                if (b->launch[op].nvb <= 0) break;
+                batch_grid(b, op, per_sm[pi] * (256 / blocks[bi]));
+                const float ms = batch_time_pass<T>(b, op, 3, e0, e1);
+                if (ms < 0.0f) { st = batch_fail(b, cudaErrorUnknown); break; }
+                if (best < 0.0f || ms < best) { best = ms; bb = blocks[bi]; bg = per_sm[pi] * (256 / blocks[bi]); }
+            }
+        b->launch[op].block = bb;
+        batch_table<T>(b);
+        batch_grid(b, op, bg);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != LBM_OK) return st;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return batch_fail(b, cudaErrorUnknown);
+    b->graph_ok = false;   // launch shapes changed: the next step captures again
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (config)
+        for (int op = 0; op < 3; ++op) {
+            config[2 * op] = b->launch[op].block;
+            config[2 * op + 1] = b->launch[op].grid;
+        }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_workspace_size(lbm_ctx* const* ctxs, int n, size_t* bytes)
+{
+    if (!ctxs || n < 1 || !bytes) return LBM_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return LBM_ERR_INVALID_ARG;
+        if (!batch_compatible(ctxs[0], ctxs[i])) return LBM_ERR_INVALID_ARG;
+    }
+    *bytes = align256(batch_item_bytes(ctxs[0]) * (size_t)n);
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, void* d_workspace, size_t bytes, void* stream,
+                            lbm_batch** out)
+{
+    if (!out) return LBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    size_t need = 0;
+    const lbm_status s = lbm_batch_workspace_size(ctxs, n, &need);
+    if (s != LBM_OK) return s;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < i; ++j)
+            if (ctxs[i] == ctxs[j]) return LBM_ERR_INVALID_ARG;   // each lattice once
+    if (!d_workspace || bytes < need || ((uintptr_t)d_workspace & 255)) return LBM_ERR_WORKSPACE;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        return LBM_ERR_CUDA;
+    lbm_batch* b = new (std::nothrow) lbm_batch();
+    if (!b) return LBM_ERR_INVALID_ARG;
+    b->ctx.assign(ctxs, ctxs + n);
+    b->stream = (cudaStream_t)stream;
+    b->launch_on = b->stream;
+    if (cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess) {
+        delete b;
+        return LBM_ERR_CUDA;
+    }
+    b->ws = (char*)d_workspace;
+    b->ws_bytes = bytes;
+    b->exec = nullptr;
+    b->graph_ok = false;
+    b->launches = 0;
+    b->sms = sms;
+    for (int op = 0; op < 3; ++op) b->launch[op].block = 256;
+    if (ctxs[0]->elt == 8) batch_table<double>(b);
+    else batch_table<float>(b);
+    batch_grid(b, BOP_DENSITY, 6);
+    batch_grid(b, BOP_VIRTUAL, 6);
+    batch_grid(b, BOP_COLLIDE, 4);
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_autotune(lbm_batch* b, int* config)
+{
+    if (!b) return LBM_ERR_INVALID_ARG;
+    for (lbm_ctx* c : b->ctx) {
+        if (c->sticky != LBM_OK) return c->sticky;
+        if (!ready(c)) return LBM_ERR_STATE;
+    }
+    return b->ctx[0]->elt == 8 ? batch_autotune_t<double>(b, config) : batch_autotune_t<float>(b, config);
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int nsteps)
+{
+    if (!b || nsteps < 0) return LBM_ERR_INVALID_ARG;
+    for (lbm_ctx* c : b->ctx) {
+        if (c->sticky != LBM_OK) return c->sticky;
+        if (!ready(c)) return LBM_ERR_STATE;
+    }
+    if (nsteps == 0) return LBM_OK;
+    return b->ctx[0]->elt == 8 ? batch_step_t<double>(b, nsteps) : batch_step_t<float>(b, nsteps);
+}
+
+long long lbm_batch_launches(const lbm_batch* b) { return b ? b->launches : -1; }
+
+void lbm_batch_destroy(lbm_batch* b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->capture) cudaStreamDestroy(b->capture);
+    delete b;
+}
+
 const char* lbm_status_str(lbm_status s)
 {
     switch (s) {

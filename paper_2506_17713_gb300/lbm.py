@@ -29,7 +29,9 @@ LBM_HOST, LBM_DEVICE = 0, 1
 EXPORTS = ["lbm_workspace_size", "lbm_create", "lbm_set_geometry", "lbm_init_fields", "lbm_step",
            "lbm_macroscopic", "lbm_diagnostics", "lbm_get_populations", "lbm_set_populations",
            "lbm_velocity_set", "lbm_sync", "lbm_kernel_launches", "lbm_temperature", "lbm_destroy",
-           "lbm_status_str", "lbm_profile_step", "lbm_mass_noalloc"]
+           "lbm_status_str", "lbm_profile_step", "lbm_mass_noalloc", "lbm_batch_workspace_size",
+           "lbm_batch_create", "lbm_batch_autotune", "lbm_batch_step", "lbm_batch_launches",
+           "lbm_batch_destroy"]
 
 
 class LbmError(RuntimeError):
@@ -85,12 +87,21 @@ def library():
     L.lbm_temperature.argtypes = [vp, C.c_int, dp]
     L.lbm_profile_step.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_longlong)]
     L.lbm_mass_noalloc.argtypes = [pp, vp, dp, vp]
+    L.lbm_batch_workspace_size.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(sz)]
+    L.lbm_batch_create.argtypes = [C.POINTER(vp), C.c_int, vp, sz, vp, C.POINTER(vp)]
+    L.lbm_batch_autotune.argtypes = [vp, ip]
+    L.lbm_batch_step.argtypes = [vp, C.c_int]
+    L.lbm_batch_launches.argtypes = [vp]
+    L.lbm_batch_launches.restype = C.c_longlong
+    L.lbm_batch_destroy.argtypes = [vp]
+    L.lbm_batch_destroy.restype = None
     L.lbm_destroy.argtypes = [vp]
     L.lbm_destroy.restype = None
     L.lbm_status_str.argtypes = [C.c_int]
     L.lbm_status_str.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("lbm_kernel_launches", "lbm_destroy", "lbm_status_str"):
+        if name not in ("lbm_kernel_launches", "lbm_destroy", "lbm_status_str", "lbm_batch_launches",
+                        "lbm_batch_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -376,3 +387,72 @@ class Lattice:
 
     def temperature(self, comp=0):
         return lbm_temperature(self.ctx, comp)
+
+
+# ---------------------------------------------------------------------------
+# Batches of lattices (one persistent launch per pass for all of them)
+# ---------------------------------------------------------------------------
+
+def lbm_batch_workspace_size(ctxs):
+    arr = (C.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    n = C.c_size_t(0)
+    _check(library().lbm_batch_workspace_size(arr, len(ctxs), C.byref(n)), "lbm_batch_workspace_size")
+    return n.value
+
+
+def lbm_batch_create(ctxs, d_workspace, nbytes, stream):
+    arr = (C.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    b = C.c_void_p()
+    _check(library().lbm_batch_create(arr, len(ctxs), C.c_void_p(d_workspace), nbytes, C.c_void_p(stream),
+                                      C.byref(b)), "lbm_batch_create")
+    return b
+
+
+def lbm_batch_autotune(batch):
+    cfg = (C.c_int * 6)()
+    _check(library().lbm_batch_autotune(batch, cfg), "lbm_batch_autotune")
+    return [(cfg[2 * i], cfg[2 * i + 1]) for i in range(3)]
+
+
+def lbm_batch_step(batch, nsteps):
+    _check(library().lbm_batch_step(batch, nsteps), "lbm_batch_step")
+
+
+def lbm_batch_launches(batch):
+    return library().lbm_batch_launches(batch)
+
+
+def lbm_batch_destroy(batch):
+    library().lbm_batch_destroy(batch)
+
+
+class Batch:
+    """Lattices advanced together: one persistent launch per pass for all of them,
+    two time steps per CUDA graph replay. The lattices must outlive the batch."""
+
+    def __init__(self, lattices, stream=None):
+        import torch
+        self.lattices = list(lattices)
+        ctxs = [lat.ctx for lat in self.lattices]
+        self.nbytes = lbm_batch_workspace_size(ctxs)
+        self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else self.lattices[0].stream
+        self.batch = lbm_batch_create(ctxs, self.workspace.data_ptr(), self.nbytes, self.stream.cuda_stream)
+
+    def autotune(self):
+        """[(CTA size, grid)] chosen for the density, virtual-density and collide passes."""
+        return lbm_batch_autotune(self.batch)
+
+    def step(self, n=1):
+        lbm_batch_step(self.batch, n)
+
+    def launches(self):
+        return lbm_batch_launches(self.batch)
+
+    def close(self):
+        if getattr(self, "batch", None):
+            lbm_batch_destroy(self.batch)
+            self.batch = None
+
+    def __del__(self):
+        self.close()

@@ -195,7 +195,8 @@ def sphere_pack(shape_xyz, rmin, rmax, porosity, seed, max_spheres=10 ** 6):
     u = uniform(seed, 4 * 65536)
     t = 0
     count = 0
-    while 1.0 - solid.sum() / total > porosity and count < max_spheres:
+    nsolid = 0
+    while 1.0 - nsolid / total > porosity and count < max_spheres:
         if t + 4 > u.size:
             u = uniform(seed + 1 + count, 4 * 65536)
             t = 0
@@ -209,6 +210,7 @@ def sphere_pack(shape_xyz, rmin, rmax, porosity, seed, max_spheres=10 ** 6):
         zz, yy, xx = np.meshgrid(np.arange(z0, z1), np.arange(y0, y1), np.arange(x0, x1),
                                  indexing="ij")
         inside = (xx + 0.5 - cx) ** 2 + (yy + 0.5 - cy) ** 2 + (zz + 0.5 - cz) ** 2 <= r * r
+        nsolid += int(np.count_nonzero(inside & ~solid[z0:z1, y0:y1, x0:x1]))
         solid[z0:z1, y0:y1, x0:x1] |= inside
     return solid.astype(np.uint8)
 

@@ -191,3 +191,41 @@ def porous_two_component(shape=(400, 400, 400), porosity=0.15, corr_length=6.0, 
     rho_nw = np.broadcast_to(rho_minor + (rho_major - rho_minor) * s, (nz, ny, nx)).copy()
     rho_w = np.broadcast_to(rho_minor + (rho_major - rho_minor) * (1.0 - s), (nz, ny, nx)).copy()
     return case, dict(rho=[rho_w, rho_nw], solid=solid, seed=used_seed)
+
+
+def sphere_pack_batch(count=64, edge_lo=64, edge_hi=192, porosity=0.38, rmin=8.0, rmax=12.0, seed=2024,
+                      real="f32", T_red=0.8, wet_phi=1.1, buffer=6, width=5.0, tau=1.5):
+    """Batch of drainage samples: each a D3Q19 box with edges U[edge_lo, edge_hi]
+    (seeded per sample), an overlapping-sphere pack (radius U[rmin, rmax]) to the given
+    porosity, single-component Peng-Robinson at T_red with MRT collision (tau, energy
+    rates 1/tau as in the 256^3 droplet workload) and wetting
+    solids (virtual density, phi > 1: wetting liquid), liquid reservoir of `buffer`
+    planes at the x-min face and vapour elsewhere (tanh profile of the given width). The x faces are constant-density
+    faces: inlet liquid density raised by a per-sample capillary-pressure step
+    (0 to 2 %), outlet vapour density. The buffer planes are kept free of solids.
+    Returns a list of (case, init) pairs."""
+    from synth import sphere_pack, uniform
+    rg, rl = COEX[("PR", T_red)]
+    u = uniform(seed, 4 * count)
+    out = []
+    for s in range(count):
+        nx, ny, nz = (int(edge_lo + (edge_hi - edge_lo + 1) * u[4 * s + d]) for d in range(3))
+        nx, ny, nz = (min(v, edge_hi) for v in (nx, ny, nz))
+        solid = sphere_pack((nx, ny, nz), rmin, rmax, porosity, seed + 1 + s)
+        solid[:, :, :buffer] = 0
+        solid[:, :, nx - buffer:] = 0
+        step = 0.02 * u[4 * s + 3]
+        case = with_eos(base_case("D3Q19", (nx, ny, nz), real=real, collision="MRT",
+                                  tau=[tau, tau], mrt_rates=pr06_mrt_rates(tau),
+                                  A=[A_STAR[("PR", T_red)]] * 2, wet_phi=[wet_phi, wet_phi],
+                                  rho_lo=[rg, rg], rho_hi=[rl, rl],
+                                  bc=["pressure", "pressure", "periodic", "periodic", "periodic", "periodic"]),
+                        "PR", T_red, comps=(0,))
+        bc_rho = [[0.0, 0.0] for _ in range(6)]
+        bc_rho[0] = [rl * (1.0 + step), rl * (1.0 + step)]
+        bc_rho[1] = [rg, rg]
+        case["bc_rho"] = bc_rho
+        x = np.arange(nx, dtype=float)[None, None, :] * np.ones((nz, ny, 1))
+        rho = 0.5 * (rl + rg) - 0.5 * (rl - rg) * np.tanh(2.0 * (x - buffer) / width)
+        out.append((case, {"rho": [rho], "solid": solid}))
+    return out
