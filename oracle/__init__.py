@@ -36,6 +36,7 @@ class OrcParams(C.Structure):
         ("rho_lo", C.c_double * 2), ("rho_hi", C.c_double * 2),
         ("accel", (C.c_double * 3) * 2),
         ("face_bc", C.c_int * 6), ("face_rho", (C.c_double * 2) * 6),
+        ("kappa", C.c_double * 2),
     ]
 
 
@@ -64,6 +65,7 @@ def lib():
         L.orc_diagnostics.argtypes = [vp, dp, dp]
         L.orc_boundary_solids.argtypes = [vp, up]
         L.orc_interaction_force.argtypes = [vp, dp, dp, dp, C.c_int, dp]
+        L.orc_surface_Q.argtypes = [vp, dp, C.c_long, C.c_int, dp]
         L.orc_collide_single.argtypes = [vp, C.c_int, dp, dp, dp]
         L.orc_eos_Tc.restype = C.c_double
         L.orc_eos_Tc.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double]
@@ -148,6 +150,9 @@ def params_from_case(case):
     for f in range(6):
         for k in range(2):
             p.face_rho[f][k] = br[f, k]
+    kap = case.get("kappa", [0.0, 0.0])
+    for k in range(2):
+        p.kappa[k] = float(kap[k] if k < len(kap) else kap[0])
     return p
 
 
@@ -252,6 +257,15 @@ class OracleSim:
         F = np.zeros((self.K,) + self.shape + (3,))
         lib().orc_interaction_force(self.h, _dp(psi), _dp(U), _dp(rho), int(with_body), _dp(F))
         return F
+
+    def surface_Q(self, psi, node, k=0):
+        """(Qxx, Qyy, Qxy) of the surface-tension adjustment at node (x, y) from a given
+        psi field [K, nz, ny, nx] (Section 2.3)."""
+        psi = np.ascontiguousarray(np.asarray(psi, dtype=np.float64).reshape((self.K,) + self.shape))
+        x, y = node
+        out = np.zeros(3)
+        lib().orc_surface_Q(self.h, _dp(psi), int(x + self.shape[2] * y), k, _dp(out))
+        return out
 
     def collide_single(self, f, F, k=0):
         fin = np.ascontiguousarray(np.asarray(f, dtype=np.float64))

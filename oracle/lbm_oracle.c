@@ -69,6 +69,7 @@ typedef struct {
     double accel[2][3];
     int face_bc[6]; /* -x, +x, -y, +y, -z, +z */
     double face_rho[6][2];
+    double kappa[2];  /* surface-tension adjustment (Section 2.3, D2Q9 MRT only); 0 = off */
 } orc_params;
 
 typedef struct {
@@ -787,11 +788,56 @@ static void fields_and_force(orc_sim* s)
     orc_interaction_force(s, s->psi, s->U, s->rho, 1, s->F);
 }
 
+/* Source term C of the surface-tension adjustment (Section 2.3, Eq. mrt_surface and
+ * Eq. li_surface_adjust), D2Q9 moment order (rho, e, eps, jx, qx, jy, qy, pxx, pxy):
+ *   C = [0, 1.5 s_e (Qxx + Qyy), -1.5 s_eps (Qxx + Qyy), 0, 0, 0, 0, -s_nu (Qxx - Qyy), -s_nu Qxy]
+ * with the pressure-tensor term
+ *   Q = kappa (g_kk / 2) [ (1 - A) psi(x) sum_i G_i (psi(x + e_i) - psi(x)) e_i e_i
+ *                          + (A / 2) sum_i G_i (psi(x + e_i)^2 - psi(x)^2) e_i e_i ],
+ * G_i = w_i / c_s^2 the force weights. The factor g_kk / 2 is that of Li et al. (2013),
+ * whose scheme the paper implements; with it the surface tension scales with 1 - kappa
+ * as the paper states (pinned by the Laplace tests). Zero unless D2Q9, MRT, kappa != 0. */
+/* Q = (Qxx, Qyy, Qxy) at node n from the psi field psi [K][N] (Q as defined above) */
+void orc_surface_Q(const orc_sim* s, const double* psi, long n, int k, double* Qout)
+{
+    int c[3];
+    coords_of(s, n, c);
+    const double px = psi[(long)k * s->N + n], A = s->p.A[k];
+    double q[2][2] = {{0, 0}, {0, 0}};
+    for (int i = 0; i < s->Q; ++i) {
+        if (s->e[i][0] == 0 && s->e[i][1] == 0 && s->e[i][2] == 0) continue;
+        const long m = stencil_neighbour(s, c, s->e[i]);
+        const double pn = psi[(long)k * s->N + m];
+        const double G = s->w[i] / CS2;
+        const double t = (1.0 - A) * px * (pn - px) + 0.5 * A * (pn * pn - px * px);
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) q[a][b] += G * t * s->e[i][a] * s->e[i][b];
+    }
+    const double f = s->p.kappa[k] * 0.5 * s->p.g[k][k];
+    Qout[0] = f * q[0][0];
+    Qout[1] = f * q[1][1];
+    Qout[2] = f * q[0][1];
+}
+
+static void surface_source(const orc_sim* s, long n, int k, double* C)
+{
+    for (int a = 0; a < s->Q; ++a) C[a] = 0.0;
+    if (s->p.dim != 2 || s->p.collision != ORC_MRT || s->p.kappa[k] == 0.0) return;
+    double Q[3];
+    orc_surface_Q(s, s->psi, n, k, Q);
+    const double Qxx = Q[0], Qyy = Q[1], Qxy = Q[2];
+    const double se = s->rates[k][1], seps = s->rates[k][2], snu = s->rates[k][7];
+    C[1] = 1.5 * se * (Qxx + Qyy);
+    C[2] = -1.5 * seps * (Qxx + Qyy);
+    C[7] = -snu * (Qxx - Qyy);
+    C[8] = -snu * Qxy;
+}
+
 /* (5)+(6) collision of one node, one component.
  * fin: Q post-stream populations; u_eq: equilibrium velocity; dU = F/rho;
- * rates: per-moment relaxation rates (MRT) or NULL with omega (BGK). */
+ * Cm: moment-space source (MRT, may be NULL). */
 static void collide_node(const orc_sim* s, const double* fin, double rho, const double* ueq,
-                         const double* dU, int k, double* fout)
+                         const double* dU, int k, const double* Cm, double* fout)
 {
     int Q = s->Q;
     double fe[ORC_MAXQ], neq[ORC_MAXQ];
@@ -804,7 +850,7 @@ static void collide_node(const orc_sim* s, const double* fin, double rho, const 
         for (int a = 0; a < Q; ++a) {
             double acc = 0.0;
             for (int i = 0; i < Q; ++i) acc += s->M[a][i] * neq[i];
-            m[a] = s->rates[k][a] * acc;
+            m[a] = s->rates[k][a] * acc - (Cm ? Cm[a] : 0.0);   /* f* = f - M^-1 (S m_neq - C) */
         }
         for (int i = 0; i < Q; ++i) {
             double acc = 0.0;
@@ -828,7 +874,7 @@ void orc_collide_single(const orc_sim* s, int k, const double* fin, const double
     }
     double u[3] = {j[0] / rho, j[1] / rho, j[2] / rho};
     double dU[3] = {F[0] / rho, F[1] / rho, F[2] / rho};
-    collide_node(s, fin, rho, u, dU, k, fout);
+    collide_node(s, fin, rho, u, dU, k, NULL, fout);
 }
 
 static void collide(orc_sim* s)
@@ -857,7 +903,9 @@ static void collide(orc_sim* s)
                 u[a] = (s->p.common_velocity && K > 1) ? ucommon[a] : jn[a] / r;
                 dU[a] = Fn[a] / r;
             }
-            collide_node(s, s->f + ((long)k * N + n) * Q, r, u, dU, k,
+            double Cm[ORC_MAXQ];
+            surface_source(s, n, k, Cm);
+            collide_node(s, s->f + ((long)k * N + n) * Q, r, u, dU, k, Cm,
                          s->fpost + ((long)k * N + n) * Q);
         }
     }
