@@ -130,6 +130,14 @@ typedef struct lbm_params {
     int schedule;    /* LBM_SCHEDULE_AUTO | _TWO_PASS | _SINGLE_PASS | _SLAB_OVERLAP */
     double rho_ref[2]; /* LBM_FP16S / LBM_BF16S: reference density of the stored deviation
                           f_i - w_i rho_ref[k] (1 = the lattice weights); ignored otherwise */
+    double kappa[2];   /* surface-tension adjustment (Section 2.3, Eqs. mrt_surface and
+                          li_surface_adjust): the MRT collision gains the moment source
+                          C = [0, 1.5 s_e (Qxx+Qyy), -1.5 s_eps (Qxx+Qyy), 0, 0, 0, 0,
+                          -s_nu (Qxx-Qyy), -s_nu Qxy] with
+                          Q = kappa g_kk/2 [(1-A) psi sum_i G_i (psi(x+e_i)-psi) e_i e_i
+                                            + A/2 sum_i G_i (psi(x+e_i)^2-psi^2) e_i e_i].
+                          0 = off. Nonzero only with D2Q9 and MRT (the paper gives no D3Q19
+                          form): LBM_ERR_INVALID_ARG otherwise. */
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx;

@@ -72,6 +72,7 @@ struct Params {
     T wet_phi[2], wet_drho[2], rho_min[2], rho_max[2];
     T accel[2][3];
     T rho_ref[2];        // 16-bit population storage holds f_i - w_i rho_ref[k] (0 otherwise)
+    T kappa_g2[2];       // kappa g_kk / 2 of the surface-tension source (D2Q9 MRT; 0 = off)
     T bc_rho[2][2];      // [x side][component]
 };
 

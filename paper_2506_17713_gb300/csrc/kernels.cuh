@@ -759,6 +759,41 @@ LBM_HD void interaction_force(const KArgs<T>& a, const Node& nd, const Geo3& g, 
     interaction_force_at<L, T, K, EXACT>(a.p, at, rho, F);
 }
 
+// Moment source C of the surface-tension adjustment (Section 2.3, Eq. mrt_surface and
+// Eq. li_surface_adjust) for D2Q9, entries 1, 2, 7, 8 of the moment vector
+// (rho, e, eps, jx, qx, jy, qy, pxx, pxy); the rest are zero:
+//   C_e = 1.5 s_e (Qxx + Qyy), C_eps = -1.5 s_eps (Qxx + Qyy),
+//   C_pxx = -s_nu (Qxx - Qyy), C_pxy = -s_nu Qxy,
+//   Q = kappa g_kk/2 [(1 - A) psi(x) sum_i G_i (psi(x+e_i) - psi(x)) e_i e_i
+//                     + A/2 sum_i G_i (psi(x+e_i)^2 - psi(x)^2) e_i e_i],
+// with the force weights G_i = w_i / c_s^2 and the clamped stencil of the force.
+template <class L, typename T, class PsiAt>
+LBM_HD void surface_source(const Params<T>& P, const PsiAt& psi_at, int k, T (&C)[L::Q])
+{
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) C[a] = T(0);
+    if (P.kappa_g2[k] == T(0)) return;
+    const T px = psi_at(k, 0, 0, 0), A = P.A[k];
+    T qxx = T(0), qyy = T(0), qxy = T(0);
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+        const T pn = psi_at(k, L::ex(i), L::ey(i), L::ez(i));
+        const T t = T(3.0 * L::w(i)) * ((T(1) - A) * px * (pn - px) + T(0.5) * A * (pn * pn - px * px));
+        if (L::ex(i)) qxx += t;
+        if (L::ey(i)) qyy += t;
+        if (L::ex(i) && L::ey(i)) qxy += L::ex(i) * L::ey(i) > 0 ? t : -t;
+    }
+    const T kg = P.kappa_g2[k];
+    qxx *= kg;
+    qyy *= kg;
+    qxy *= kg;
+    const T se = P.rates[k][1], seps = P.rates[k][2], snu = P.omega[k];
+    C[1] = T(1.5) * se * (qxx + qyy);
+    C[2] = T(-1.5) * seps * (qxx + qyy);
+    C[7] = -snu * (qxx - qyy);
+    C[8] = -snu * qxy;
+}
+
 // ---------------------------------------------------------------------------
 // Collision (Eq. collision_model) with EDM forcing (Eq. edm)
 // ---------------------------------------------------------------------------
@@ -923,8 +958,10 @@ LBM_HD void collide_mrt_d3q19(const Params<T>& P, int k, T (&f)[19], T rho, cons
 // as f_i + (small correction) so that only one rounding lands on f_i. BGK adds
 // the EDM shift per direction; MRT adds it in moment space together with the
 // relaxation, f* = f + M^-1 (Delta m^eq - S m^neq).
+// Cm (may be null): moment source added to the relaxation, f* = f - M^-1 (S m_neq - C)
 template <class L, typename T, int COLL>
-LBM_HD void collide(const Params<T>& P, int k, T (&f)[L::Q], T rho, const T (&u)[3], const T (&du)[3])
+LBM_HD void collide(const Params<T>& P, int k, T (&f)[L::Q], T rho, const T (&u)[3], const T (&du)[3],
+                    const T* Cm = nullptr)
 {
     if constexpr (COLL != COLL_BGK && L::Q == 19) {
         collide_mrt_d3q19<T>(P, k, f, rho, u, du);
@@ -1009,7 +1046,8 @@ LBM_HD void collide(const Params<T>& P, int k, T (&f)[L::Q], T rho, const T (&u)
                     });
                 }
                 const T s = L::stress(a) ? P.omega[k] : P.rates[k][a];
-                m[a] = fma(-s, acc, dm) * T(inv_norm);
+                const T cm = Cm ? Cm[a] : T(0);
+                m[a] = (fma(-s, acc, dm) + cm) * T(inv_norm);
             }
         });
         // f* = f + M^-1 (Delta m^eq - S m^neq), M^-1 = M^T diag(1 / row norm)
@@ -1139,6 +1177,20 @@ __device__ __forceinline__ void collide_node(const KArgs<T>& a, const Node& nd)
         for (int k = 0; k < K; ++k) moments<L, T>(f[k], rho[k], j[k]);
         interaction_force<L, T, K, !pop_shifted<T, S>>(a, nd, geo3<GEOM>(P, nd.x, nd.y, nd.z), rho, F);
     }
+    // surface-tension adjustment (D2Q9 MRT, kappa != 0)
+    T Cm[K][L::Q];
+    bool use_c = false;
+    if constexpr (L::D == 2 && COLL == COLL_MRT) {
+        const Geo3 gq = geo3<GEOM>(P, nd.x, nd.y, nd.z);
+        auto at = [&](int kk, int ex, int ey, int ez) -> T {
+            return a.psi[(long long)kk * N + stencil_index(gq, ex, ey, ez)];
+        };
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            surface_source<L, T>(P, at, kk, Cm[kk]);
+            use_c |= P.kappa_g2[kk] != T(0);
+        }
+    }
     T uc[3] = {T(0), T(0), T(0)};
     if (K > 1 && P.common_velocity) {
         T den = T(0);
@@ -1160,7 +1212,7 @@ __device__ __forceinline__ void collide_node(const KArgs<T>& a, const Node& nd)
             u[d] = (K > 1 && P.common_velocity) ? uc[d] : j[k][d] * inv;
             du[d] = F[k][d] * inv;
         }
-        collide<L, T, COLL>(P, k, f[k], rho[k], u, du);
+        collide<L, T, COLL>(P, k, f[k], rho[k], u, du, use_c ? Cm[k] : nullptr);
         S* dst = static_cast<S*>(a.f_dst) + (long long)k * L::Q * N + nd.n;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) store_pop<L, T, S>(dst, (long long)i * N, i, f[k][i], P.rho_ref[k]);

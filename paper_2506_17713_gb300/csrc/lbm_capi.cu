@@ -203,6 +203,10 @@ lbm_status validate(const lbm_params* p)
             if (p->bc[f] == LBM_BC_PRESSURE && !(p->bc_rho[f][k] > 0)) return LBM_ERR_INVALID_ARG;
     }
     if (p->ncomp == 2 && p->g[0][1] != p->g[1][0]) return LBM_ERR_INVALID_ARG;
+    for (int k = 0; k < p->ncomp; ++k) {
+        if (!fin(p->kappa[k])) return LBM_ERR_INVALID_ARG;
+        if (p->kappa[k] != 0.0 && (p->lattice != LBM_D2Q9 || p->collision != LBM_MRT)) return LBM_ERR_INVALID_ARG;
+    }
     if (p->schedule != LBM_SCHEDULE_AUTO && p->schedule != LBM_SCHEDULE_TWO_PASS &&
         p->schedule != LBM_SCHEDULE_SINGLE_PASS && p->schedule != LBM_SCHEDULE_SLAB_OVERLAP)
         return LBM_ERR_INVALID_ARG;
@@ -318,6 +322,7 @@ void fill_params(const lbm_ctx* c, Params<T>& P)
         for (int d = 0; d < 3; ++d) P.accel[k][d] = (T)((d2 && d == 2) ? 0.0 : p->body_accel[kk][d]);
         for (int s = 0; s < 2; ++s) P.bc_rho[s][k] = (T)p->bc_rho[s][kk];
         P.rho_ref[k] = (p->real == LBM_FP16S || p->real == LBM_BF16S) ? (T)p->rho_ref[kk] : T(0);
+        P.kappa_g2[k] = (T)(p->kappa[kk] * 0.5 * p->g[kk][kk]);
     }
 }
 

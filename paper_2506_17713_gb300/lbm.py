@@ -55,6 +55,7 @@ class lbm_params(C.Structure):
         ("bc", C.c_int * 6), ("bc_rho", (C.c_double * 2) * 6),
         ("schedule", C.c_int),
         ("rho_ref", C.c_double * 2),
+        ("kappa", C.c_double * 2),
     ]
 
 
@@ -234,8 +235,10 @@ def params_from_case(case):
     p.ncomp = int(case.get("ncomp", 1))
     p.real = {"f32": LBM_FP32, "f64": LBM_FP64, "f16s": LBM_FP16S, "bf16s": LBM_BF16S}[case.get("real", "f32")]
     rr = case.get("rho_ref", [1.0, 1.0])
+    kap = case.get("kappa", [0.0, 0.0])
     for k in range(2):
         p.rho_ref[k] = float(rr[k] if k < len(rr) else rr[0])
+        p.kappa[k] = float(kap[k] if k < len(kap) else kap[0])
     p.collision = LBM_MRT if case.get("collision", "BGK") == "MRT" else LBM_BGK
     p.velocity = LBM_UEQ_COMMON if case.get("velocity", "component") == "common" else LBM_UEQ_COMPONENT
     p.tau[:] = _two(case.get("tau"), 1.0)

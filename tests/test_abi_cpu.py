@@ -77,6 +77,7 @@ def test_workspace_size_layout(lib):
     dict(T_red=[0.0, 0.0]),
     dict(shape=(2048, 1024, 1024)),            # 2^31 nodes: node indices are 32-bit
     dict(real="f16s", rho_ref=[float("nan"), 1.0]),
+    dict(kappa=[0.5, 0.5]),                    # surface-tension source: D2Q9 MRT only
 ])
 def test_rejects_invalid_parameters(lib, bad):
     from paper_2506_17713_gb300 import lbm

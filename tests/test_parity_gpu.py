@@ -218,6 +218,34 @@ def test_d2q9_walls_body_force_fp32():
     compare(lat, orc, tol32(300))
 
 
+@pytest.mark.parametrize("real,steps", [("f64", 300), ("f32", 100)])
+def test_surface_tension_adjustment_kappa_d2q9(real, steps):
+    # Section 2.3: MRT with the moment source C (kappa = 0.5), CS droplet
+    case, init = cases.droplet_2d_cs(n=64, radius=14.0, real=real)
+    case["collision"] = "MRT"
+    case["kappa"] = [0.5, 0.5]
+    lat, orc = run_both(case, init["rho"], steps)
+    compare(lat, orc, TOL64 if real == "f64" else tol32(steps))
+
+
+def test_surface_tension_adjustment_with_walls_and_solids():
+    shape = (48, 40, 1)
+    case = cases.with_eos(cases.base_case("D2Q9", shape, collision="MRT", real="f64",
+                                          A=[cases.A_STAR[("CS", 0.7)]] * 2, kappa=[0.3, 0.3],
+                                          wet_phi=[1.1, 1.1],
+                                          bc=["periodic", "periodic", "wall", "wall", "periodic", "periodic"]),
+                          "CS", 0.7)
+    case["eos_a"] = [0.5, 0.5]
+    rg, rl = cases.COEX[("CS", 0.7)]
+    case["rho_lo"] = [rg, rg]
+    case["rho_hi"] = [rl, rl]
+    rho = droplet_field(shape, [(24.0, 14.0)], [10.0], rl, rg, 5.0, periodic=False)
+    solid = np.zeros((1, 40, 48), dtype=np.uint8)
+    solid[0, 0:3, :] = 1
+    lat, orc = run_both(case, [rho], 200, solid=solid)
+    compare(lat, orc, TOL64)
+
+
 def test_virtual_density_values_at_solids():
     # psi at boundary solids is the same on both sides: compared through the
     # force-driven velocity next to the wall after one step
