@@ -75,7 +75,8 @@ def algorithmic_bytes(case, fused=False, fluid_list=False):
     each value once). Two-pass schedule -- collide: read K*Q populations + K psi
     [+ 1 B mask], write K*Q populations; density: read K*Q populations [+ 1 B mask],
     write K psi [+ K rho next to solids]. With solids the kernels run over the fluid-node
-    list: the units are fluid nodes and each also reads its 4 B list entry. Single-pass
+    list: the units are fluid nodes, whose populations sit at fluid slots, and each reads
+    its 4 B list entry and 4 B node -> slot map entry instead of the mask. Single-pass
     schedule (k_fused): read and write K*Q populations."""
     Q = 19 if case["lattice"] == "D3Q19" else 9
     e = 8 if case.get("real") == "f64" else 4                       # scalars (psi, rho)
@@ -84,9 +85,11 @@ def algorithmic_bytes(case, fused=False, fluid_list=False):
     geom = any(b != "periodic" for b in case.get("bc", ["periodic"] * 6)) or fluid_list
     if fused:
         return {"collide": 2 * K * Q * ep, "density": 0, "step": 2 * K * Q * ep}
-    lst = 4 if fluid_list else 0
-    collide = 2 * K * Q * ep + K * e + (1 if geom else 0) + lst
-    density = K * Q * ep + K * e + (K * e + 1 if geom else 0) + lst
+    # with solids: populations at fluid slots, a 4 B list entry and a 4 B node -> slot map
+    # entry per fluid node replace the 1 B mask
+    lst, mask = (8, 0) if fluid_list else (0, 1 if geom else 0)
+    collide = 2 * K * Q * ep + K * e + mask + lst
+    density = K * Q * ep + K * e + (K * e + mask if geom else 0) + lst
     return {"collide": collide, "density": density, "step": collide + density}
 
 

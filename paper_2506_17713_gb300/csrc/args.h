@@ -101,6 +101,8 @@ struct KArgs {
     int n_bsolid;
     const int* fluid;    // fluid node list (ascending), or null: kernels run over every node
     int n_fluid;
+    const int* fidx;     // with the fluid list: node -> fluid index (-1 at solids), the slot of the
+                         // node's populations (fluid-only storage); null: slot = node index
     int geom;            // solids present or a non-periodic face
     int* status;         // device status word
     // operation-specific

@@ -334,9 +334,13 @@ LBM_HD void store_pop(S* __restrict__ p, long long m, int i, T v, T rho_ref)
 // Node addressing
 // ---------------------------------------------------------------------------
 
+// A node and the slot of its populations: the node index n, or -- on lattices with
+// solids, whose populations are stored for fluid nodes only, in fluid-list order --
+// its fluid index.
 struct Node {
     int x, y, z;
     long long n;
+    long long slot = -1;
 };
 
 __device__ __forceinline__ bool node_of_thread(int nx, int ny, Node& nd, int z0 = 0)
@@ -362,6 +366,7 @@ __device__ __forceinline__ bool node_of_list(const KArgs<T>& a, Node& nd)
     nd.y = (int)(yz - z * (uint32_t)a.p.ny);
     nd.z = (int)z;
     nd.n = (long long)n;
+    nd.slot = t;
     return true;
 }
 
@@ -561,9 +566,12 @@ LBM_HD int stencil_index(const Geo3& g, int ex, int ey, int ez)
 // with halfway bounce-back): the pull decision of each direction -- regular source,
 // bounce-back at a wall face or solid node, or unknown across a constant-density face
 // (completed by Zou-He) -- is taken once and applied to every component.
+// With fidx (lattices with solids: fluid-only population storage) a source node m
+// holds its populations at slot fidx[m], and fidx[m] < 0 marks a solid.
 template <class L, typename T, typename S, int K, bool GEOM>
 LBM_HD void gather_all(const void* f_all, const Params<T>& P, const uint8_t* __restrict__ solid,
-                       const Node& nd, const Geo3& g, T (&f)[K][L::Q], int k0 = 0)
+                       const int* __restrict__ fidx, const Node& nd, const Geo3& g, T (&f)[K][L::Q],
+                       int k0 = 0)
 {
     const long long N = P.N;
     const S* fs = static_cast<const S*>(f_all) + (long long)k0 * L::Q * N;
@@ -577,8 +585,20 @@ LBM_HD void gather_all(const void* f_all, const Params<T>& P, const uint8_t* __r
         } else {
             const unsigned face = i == 0 ? 0u : pull_face(g, L::ex(i), L::ey(i), L::ez(i));
             const bool unknown = (face & 2u) != 0u;   // constant-density x face (precedence)
-            const bool bounce = !unknown && (face == 1u || (i != 0 && solid[src]));
-            const long long m = bounce ? (long long)L::opp(i) * N + nd.n : (long long)i * N + src;
+            long long self, from;
+            bool is_solid;
+            if (fidx) {
+                self = nd.slot;
+                const int js = i == 0 ? (int)nd.slot : fidx[src];
+                is_solid = js < 0;
+                from = js;
+            } else {
+                self = nd.n;
+                is_solid = i != 0 && solid[src];
+                from = src;
+            }
+            const bool bounce = !unknown && (face == 1u || is_solid);
+            const long long m = bounce ? (long long)L::opp(i) * N + self : (long long)i * N + from;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 const T v = load_pop<L, T, S>(fs, (long long)k * L::Q * N + m, i, P.rho_ref[k0 + k]);
@@ -599,10 +619,10 @@ LBM_HD void gather_all(const void* f_all, const Params<T>& P, const uint8_t* __r
 
 template <class L, typename T, typename S, bool GEOM>
 LBM_HD void gather_k(const void* f_all, const Params<T>& P, const uint8_t* __restrict__ solid, const Node& nd,
-                     int k, T (&f)[L::Q])
+                     int k, T (&f)[L::Q], const int* fidx = nullptr)
 {
     T fk[1][L::Q];
-    gather_all<L, T, S, 1, GEOM>(f_all, P, solid, nd, geo3<GEOM>(P, nd.x, nd.y, nd.z), fk, k);
+    gather_all<L, T, S, 1, GEOM>(f_all, P, solid, fidx, nd, geo3<GEOM>(P, nd.x, nd.y, nd.z), fk, k);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) f[i] = fk[0][i];
 }
@@ -1098,7 +1118,7 @@ __device__ __forceinline__ void density_node(const KArgs<T>& a, const Node& nd)
     const long long N = a.p.N;
     bool bad = false, clamp = false;
     T f[K][L::Q];
-    gather_all<L, T, S, K, GEOM>(a.f_src, a.p, a.solid, nd, geo3<GEOM>(a.p, nd.x, nd.y, nd.z), f);
+    gather_all<L, T, S, K, GEOM>(a.f_src, a.p, a.solid, a.fidx, nd, geo3<GEOM>(a.p, nd.x, nd.y, nd.z), f);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const T r = density<L, T>(f[k]);
@@ -1165,14 +1185,14 @@ __device__ __forceinline__ void collide_node(const KArgs<T>& a, const Node& nd)
     if constexpr (GEOM) {
         // lattices with solids or closed faces: one table for the pull and the force stencil
         const Geo3 g = geo3<GEOM>(P, nd.x, nd.y, nd.z);
-        gather_all<L, T, S, K, GEOM>(a.f_src, P, a.solid, nd, g, f);
+        gather_all<L, T, S, K, GEOM>(a.f_src, P, a.solid, a.fidx, nd, g, f);
 #pragma unroll
         for (int k = 0; k < K; ++k) moments<L, T>(f[k], rho[k], j[k]);
         interaction_force<L, T, K, !pop_shifted<T, S>>(a, nd, g, rho, F);
     } else {
         // periodic: the wrapped offsets are cheap to form again, which keeps them out of
         // the registers live across the moments (64 per thread here)
-        gather_all<L, T, S, K, GEOM>(a.f_src, P, a.solid, nd, geo3<GEOM>(P, nd.x, nd.y, nd.z), f);
+        gather_all<L, T, S, K, GEOM>(a.f_src, P, a.solid, a.fidx, nd, geo3<GEOM>(P, nd.x, nd.y, nd.z), f);
 #pragma unroll
         for (int k = 0; k < K; ++k) moments<L, T>(f[k], rho[k], j[k]);
         interaction_force<L, T, K, !pop_shifted<T, S>>(a, nd, geo3<GEOM>(P, nd.x, nd.y, nd.z), rho, F);
@@ -1213,7 +1233,7 @@ __device__ __forceinline__ void collide_node(const KArgs<T>& a, const Node& nd)
             du[d] = F[k][d] * inv;
         }
         collide<L, T, COLL>(P, k, f[k], rho[k], u, du, use_c ? Cm[k] : nullptr);
-        S* dst = static_cast<S*>(a.f_dst) + (long long)k * L::Q * N + nd.n;
+        S* dst = static_cast<S*>(a.f_dst) + (long long)k * L::Q * N + (a.fidx ? nd.slot : nd.n);
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) store_pop<L, T, S>(dst, (long long)i * N, i, f[k][i], P.rho_ref[k]);
     }
@@ -1358,7 +1378,8 @@ __global__ void __launch_bounds__(256) k_unstream(const KArgs<T> a)
     const Params<T>& P = a.p;
     const long long N = P.N;
     const T rr = P.rho_ref[a.comp];
-    S* dst = static_cast<S*>(a.f_dst) + (long long)a.comp * L::Q * N + nd.n;
+    if (a.fidx && a.fidx[nd.n] < 0) return;   // fluid-only storage: solids have no slot
+    S* dst = static_cast<S*>(a.f_dst) + (long long)a.comp * L::Q * N + (a.fidx ? a.fidx[nd.n] : nd.n);
     if (GEOM && a.solid[nd.n]) {   // never read; stored as zero deviation
 #pragma unroll
         for (int i = 0; i < L::Q; ++i)
@@ -1400,7 +1421,8 @@ __global__ void __launch_bounds__(256) k_get_pops(const KArgs<T> a)
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) f[i] = T(0);
     } else {
-        gather_k<L, T, S, GEOM>(a.f_src, a.p, a.solid, nd, a.comp, f);
+        if (a.fidx) nd.slot = a.fidx[nd.n];
+        gather_k<L, T, S, GEOM>(a.f_src, a.p, a.solid, nd, a.comp, f, a.fidx);
     }
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) a.out_f[(long long)i * N + nd.n] = f[i];
@@ -1414,7 +1436,7 @@ LBM_HD void node_macro(const KArgs<T>& a, const Node& nd, int comp, T& r_out,
     const Geo3 g = geo3<GEOM>(a.p, nd.x, nd.y, nd.z);
     T f[K][L::Q];
     T j[K][3];
-    gather_all<L, T, S, K, GEOM>(a.f_src, a.p, a.solid, nd, g, f);
+    gather_all<L, T, S, K, GEOM>(a.f_src, a.p, a.solid, a.fidx, nd, g, f);
 #pragma unroll
     for (int k = 0; k < K; ++k) moments<L, T>(f[k], rk[k], j[k]);
     T F[K][3];
@@ -1442,6 +1464,7 @@ __global__ void __launch_bounds__(256) k_macro(const KArgs<T> a)
     const long long N = a.p.N;
     T r = T(0), u[3] = {T(0), T(0), T(0)};
     if (!(GEOM && a.solid[nd.n])) {
+        if (a.fidx) nd.slot = a.fidx[nd.n];
         T rk[K], mk[K][3];
         node_macro<L, T, S, K, GEOM>(a, nd, a.comp, r, u, rk, mk);
     }
@@ -1492,6 +1515,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag(const KArgs<T> a)
         nd.y = (int)((n / P.nx) % P.ny);
         nd.z = (int)(n / ((long long)P.nx * P.ny));
         if (GEOM && a.solid[n]) continue;
+        if (a.fidx) nd.slot = a.fidx[n];
         T r, u[3], rk[K], mk[K][3];
         node_macro<L, T, S, K, GEOM>(a, nd, -1, r, u, rk, mk);
         if (a.want_residual) {
@@ -1579,6 +1603,7 @@ __device__ __forceinline__ bool node_of_unit(const KArgs<T>& a, long long t, Nod
         if (t >= a.p.N) return false;
         n = (uint32_t)t;
     }
+    nd.slot = t;
     const uint32_t yz = fast_div(n, a.p.div_nx);
     const uint32_t z = fast_div(yz, a.p.div_ny);
     nd.x = (int)(n - yz * (uint32_t)a.p.nx);

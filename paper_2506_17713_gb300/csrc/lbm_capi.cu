@@ -36,6 +36,8 @@ struct lbm_ctx {
     int n_bsolid;
     int* fluid;
     int n_fluid;
+    int* fidx;              // node -> fluid index (-1 at solids); populations of lattices with
+                            // solids are stored for fluid nodes only, at that slot
     void* u_prev;
     int* status;
     double* partials;
@@ -148,7 +150,7 @@ double eos_alpha(int eos, double omega, double Tr)
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t f, psi, rho, solid, bsolid, uprev, stage, status, partials, totals, total;
+    size_t f, psi, rho, solid, bsolid, fidx, uprev, stage, status, partials, totals, total;
 };
 
 bool fin(double v) { return std::isfinite(v); }
@@ -229,6 +231,7 @@ Layout layout_of(const lbm_params* p)
     L.rho = off;      off += align256(K * N * e);
     L.solid = off;    off += align256(N);
     L.bsolid = off;   off += align256(N * sizeof(int));
+    L.fidx = off;     off += align256(N * sizeof(int));
     L.uprev = off;    off += align256((size_t)D * N * e);
     // host transfers stage in the idle population buffer; 16-bit buffers are too small
     // for (1 + D) N doubles (fields in) or Q N floats (populations in and out)
@@ -341,6 +344,7 @@ KArgs<T> base_args(lbm_ctx* c, const Params<T>& P)
     a.n_bsolid = c->n_bsolid;
     a.fluid = c->any_solid ? c->fluid : nullptr;
     a.n_fluid = c->any_solid ? c->n_fluid : 0;
+    a.fidx = c->any_solid ? c->fidx : nullptr;
     a.geom = c->geom;
     a.status = c->status;
     a.u_prev = (T*)c->u_prev;
@@ -544,6 +548,7 @@ lbm_status lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void
     c->rho = c->ws + L.rho;
     c->solid = (uint8_t*)(c->ws + L.solid);
     c->bsolid = (int*)(c->ws + L.bsolid);
+    c->fidx = (int*)(c->ws + L.fidx);
     c->u_prev = c->ws + L.uprev;
     c->status = (int*)(c->ws + L.status);
     c->partials = (double*)(c->ws + L.partials);
@@ -613,9 +618,16 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* solid, int where)
             if (!h[(size_t)n]) list.push_back((int)n);
     c->n_fluid = (int)list.size() - c->n_bsolid;
     c->fluid = c->bsolid + c->n_bsolid;
+    std::vector<int> fidx;
+    if (c->any_solid) {
+        fidx.assign((size_t)c->N, -1);
+        for (int j = 0; j < c->n_fluid; ++j) fidx[(size_t)list[(size_t)(c->n_bsolid + j)]] = j;
+    }
     e = cudaMemcpyAsync(c->solid, h.data(), (size_t)c->N, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && !list.empty())
         e = cudaMemcpyAsync(c->bsolid, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && !fidx.empty())
+        e = cudaMemcpyAsync(c->fidx, fidx.data(), sizeof(int) * fidx.size(), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return fail_cuda(c, e);
     c->geom = c->faces_open || c->any_solid;

@@ -23,8 +23,8 @@ def test_algorithmic_bytes():
     b2 = bench.algorithmic_bytes(c2)
     assert b2["collide"] == 2 * 2 * 19 * 4 + 2 * 4 + 1
     assert b2["density"] == 2 * 19 * 4 + 2 * 4 + 2 * 4 + 1
-    b3 = bench.algorithmic_bytes(c2, fluid_list=True)      # per fluid node, with its list entry
-    assert b3["collide"] == b2["collide"] + 4 and b3["density"] == b2["density"] + 4
+    b3 = bench.algorithmic_bytes(c2, fluid_list=True)      # per fluid node: list + slot map, no mask
+    assert b3["collide"] == b2["collide"] - 1 + 8 and b3["density"] == b2["density"] - 1 + 8
 
 
 def _rank(rank, world, port, q):
