@@ -31,6 +31,8 @@ WORKLOADS = {
     "exp256": "D3Q19 Shan-Chen psi=exp(-1/rho) BGK 256^3 FP32, droplet R=30",
     "porous400": "D3Q19 two-component Shan-Chen 400^3 FP32, GRF porous medium (porosity 0.15, "
                  "corr. length 6, seed 7), wetting, constant-density x faces",
+    "warmstart": "learned warm start of single-phase steady-state runs: D3Q19 BGK, periodic GRF porous "
+                 "samples (porosity U[0.1,0.35], corr. length 6), body force; 3-D U-Net trained on LBM steady states",
     "batch64": "64 D3Q19 sphere-pack drainage samples, box edges U[64,192] (seed 2024), overlapping spheres "
                "r U[8,12] to porosity 0.38, PR T=0.8Tc MRT FP32, wetting solids, per-sample inlet pressure step",
 }
@@ -376,6 +378,73 @@ def run_batch(args):
     batch.close()
 
 
+def run_warmstart(args):
+    """Time to steady state (residual <= 1e-6) of held-out samples, from the network's
+    prediction vs from rest; the network is trained in the same run on steady states
+    the LBM produces."""
+    import torch
+    from paper_2506_17713_gb300 import warmstart as ws
+    from synth import uniform
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    n, ntrain, ntest = args.ws_n, args.ws_train, args.ws_test
+    u = uniform(4242, ntrain + ntest)
+    phis = [0.10 + 0.25 * float(v) for v in u]
+    t0 = time.perf_counter()
+    solids, us, res = [], [], []
+    for b0 in range(0, ntrain, 32):
+        sl = slice(b0, min(ntrain, b0 + 32))
+        so, uu, rr = ws.steady_states(n, list(range(1000 + sl.start, 1000 + sl.stop)), phis[sl], args.ws_steps)
+        solids += so
+        us += uu
+        res += rr
+    t_data = time.perf_counter() - t0
+    net = ws.UNet(n, channels=(args.ws_c1, 2 * args.ws_c1, 4 * args.ws_c1), seed=0)
+    t0 = time.perf_counter()
+    hist = ws.train(net, solids, us, epochs=args.ws_epochs, batch=8)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    rows, ideal, pred_err = [], [], []
+    for j in range(ntest):
+        solid = ws.sample_solid(n, 5000 + j, phis[ntrain + j])
+        sp, tp, kp, _, u_plain = ws.relax(n, solid, None)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pred = ws.predict(net, solid)
+        t_inf = time.perf_counter() - t0
+        sw, tw, kw, _, _ = ws.relax(n, solid, pred)
+        rows.append((sp, tp, sw, tw + t_inf, kp, kw))
+        # bound on any velocity-only warm start: start from the converged field itself
+        ideal.append(ws.relax(n, solid, u_plain.astype(np.float64))[0])
+        pred_err.append(float(np.linalg.norm(pred - u_plain) / np.linalg.norm(u_plain)))
+    r = np.array(rows)
+    kerr = np.abs(r[:, 5] - r[:, 4]) / np.abs(r[:, 4])
+    if rank != 0:
+        return
+    line = {
+        "metric": "time-to-steady-state speedup (warm start vs plain LBM)",
+        "value": round(float(r[:, 1].sum() / r[:, 3].sum()), 3), "unit": "x", "n_gpus": world,
+        "steps": int(r[:, 2].sum()), "warmup": 0, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS["warmstart"], "edge": n, "train_samples": ntrain, "test_samples": ntest,
+                   "network": "3-D U-Net, channels %d/%d/%d, %d parameters" % (
+                       args.ws_c1, 2 * args.ws_c1, 4 * args.ws_c1, net.parameters()),
+                   "epochs": args.ws_epochs, "final_train_loss": round(hist[-1], 4),
+                   "train_residual_max": float(max(res)), "data_seconds": round(t_data, 1),
+                   "train_seconds": round(t_train, 1)},
+        "steps_to_steady": {"plain_mean": float(r[:, 0].mean()), "warm_mean": float(r[:, 2].mean()),
+                            "ratio": round(float(r[:, 0].sum() / r[:, 2].sum()), 3),
+                            "from_converged_velocity_mean": float(np.mean(ideal))},
+        "prediction_rel_l2_error_mean": round(float(np.mean(pred_err)), 4),
+        "wall_seconds": {"plain_total": round(float(r[:, 1].sum()), 3),
+                         "warm_total_incl_inference": round(float(r[:, 3].sum()), 3)},
+        "permeability": {"max_rel_diff_warm_vs_plain": float(kerr.max()), "plain_mean": float(r[:, 4].mean())},
+        "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import torch
     from paper_2506_17713_gb300 import Lattice, lbm
@@ -533,6 +602,12 @@ def main():
                     help="CPU time of the oracle sample behind cpu_baseline")
     ap.add_argument("--ref-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ws-n", type=int, default=48, help="warmstart: sample edge")
+    ap.add_argument("--ws-train", type=int, default=96)
+    ap.add_argument("--ws-test", type=int, default=16)
+    ap.add_argument("--ws-steps", type=int, default=16000, help="warmstart: steps of the training steady states")
+    ap.add_argument("--ws-epochs", type=int, default=40)
+    ap.add_argument("--ws-c1", type=int, default=8)
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-edge-lo", type=int, default=64)
     ap.add_argument("--batch-edge-hi", type=int, default=192)
@@ -545,6 +620,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch64":
         run_batch(args)
+    elif args.workload == "warmstart":
+        run_warmstart(args)
     else:
         run_ours(args)
 

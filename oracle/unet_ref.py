@@ -8,8 +8,9 @@ periodic), so a 3x3x3 convolution wraps around instead of padding with zeros:
   conv(x, w, b)[o, z, y, x] = b[o] + sum_{i, dz, dy, dx} w[o, i, dz+1, dy+1, dx+1]
                                      x[i, (z+dz) mod D, (y+dy) mod H, (x+dx) mod W]
 
-avg_pool2 averages 2x2x2 blocks; up2 repeats each voxel into a 2x2x2 block; the
-loss is the relative squared error sum (p - t)^2 / sum t^2.
+avg_pool2 averages 2x2x2 blocks; up2 repeats each voxel into a 2x2x2 block; relu is
+the leaky ReLU (slope 0.01 below zero); the loss is the relative squared error
+sum (p - t)^2 / sum t^2.
 """
 import numpy as np
 
@@ -45,8 +46,17 @@ def conv3d_grads(x, w, gout):
     return gx, gw, gb
 
 
+LEAK = 0.01
+
+
 def relu(x):
-    return np.maximum(x, 0.0)
+    """leaky ReLU: x for x > 0, 0.01 x otherwise"""
+    return np.where(x > 0, x, LEAK * x)
+
+
+def relu_grad(y, g):
+    """gradient through the leaky ReLU, from its output y"""
+    return np.where(y > 0, g, LEAK * g)
 
 
 def avg_pool2(x):

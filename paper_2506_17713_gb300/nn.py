@@ -1,0 +1,107 @@
+"""ctypes binding of the warm-start network kernels (include/lbm_nn.h): argument
+marshalling only. Tensors are torch CUDA float32 tensors, contiguous,
+channel-major [C, D, H, W]."""
+import ctypes as C
+
+from .lbm import LbmError, library as _lbm_library
+
+EXPORTS = ["lbm_nn_conv3d", "lbm_nn_conv3d_grad_input", "lbm_nn_conv3d_grad_weight", "lbm_nn_axpy", "lbm_nn_relu_grad",
+           "lbm_nn_avg_pool2", "lbm_nn_avg_pool2_grad", "lbm_nn_up2", "lbm_nn_up2_grad", "lbm_nn_rel_loss",
+           "lbm_nn_adam"]
+GW_SEGMENTS = 64
+
+_ready = False
+
+
+def library():
+    global _ready
+    L = _lbm_library()
+    if not _ready:
+        vp, i, ll, f = C.c_void_p, C.c_int, C.c_longlong, C.c_float
+        L.lbm_nn_conv3d.argtypes = [vp, i, i, i, i, vp, vp, i, i, vp, vp]
+        L.lbm_nn_conv3d_grad_input.argtypes = [vp, i, i, i, i, vp, i, vp, vp, vp]
+        L.lbm_nn_conv3d_grad_weight.argtypes = [vp, i, vp, i, i, i, i, vp, vp, i, vp, vp]
+        L.lbm_nn_axpy.argtypes = [vp, vp, ll, f, vp]
+        L.lbm_nn_relu_grad.argtypes = [vp, vp, ll, vp]
+        L.lbm_nn_avg_pool2.argtypes = [vp, i, i, i, i, vp, vp]
+        L.lbm_nn_avg_pool2_grad.argtypes = [vp, i, i, i, i, vp, vp]
+        L.lbm_nn_up2.argtypes = [vp, i, i, i, i, vp, vp]
+        L.lbm_nn_up2_grad.argtypes = [vp, i, i, i, i, vp, vp]
+        L.lbm_nn_rel_loss.argtypes = [vp, vp, ll, vp, vp, vp, vp]
+        L.lbm_nn_adam.argtypes = [vp, vp, vp, vp, ll, f, f, f, f, f, f, vp]
+        for n in EXPORTS:
+            getattr(L, n).restype = C.c_int
+        _ready = True
+    return L
+
+
+def _p(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _st(stream):
+    import torch
+    return C.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+
+
+def _check(s, where):
+    if s != 0:
+        raise LbmError(s, where)
+
+
+def conv3d(x, w, b, relu, y, stream=None):
+    cin, d, h, wd = x.shape
+    _check(library().lbm_nn_conv3d(_p(x), cin, d, h, wd, _p(w), _p(b), w.shape[0], int(relu), _p(y), _st(stream)),
+           "lbm_nn_conv3d")
+
+
+def conv3d_grad_input(gy, w, wt_scratch, gx, stream=None):
+    cout, d, h, wd = gy.shape
+    _check(library().lbm_nn_conv3d_grad_input(_p(gy), cout, d, h, wd, _p(w), w.shape[1], _p(wt_scratch), _p(gx),
+                                              _st(stream)), "lbm_nn_conv3d_grad_input")
+
+
+def conv3d_grad_weight(x, gy, gw, gb, accumulate, scratch, stream=None):
+    cin, d, h, wd = x.shape
+    _check(library().lbm_nn_conv3d_grad_weight(_p(x), cin, _p(gy), gy.shape[0], d, h, wd, _p(gw), _p(gb),
+                                               int(accumulate), _p(scratch), _st(stream)),
+           "lbm_nn_conv3d_grad_weight")
+
+
+def axpy(y, x, a=1.0, stream=None):
+    _check(library().lbm_nn_axpy(_p(y), _p(x), y.numel(), a, _st(stream)), "lbm_nn_axpy")
+
+
+def relu_grad(y, g, stream=None):
+    _check(library().lbm_nn_relu_grad(_p(y), _p(g), y.numel(), _st(stream)), "lbm_nn_relu_grad")
+
+
+def avg_pool2(x, y, stream=None):
+    c, d, h, w = x.shape
+    _check(library().lbm_nn_avg_pool2(_p(x), c, d, h, w, _p(y), _st(stream)), "lbm_nn_avg_pool2")
+
+
+def avg_pool2_grad(gy, gx, stream=None):
+    c, d, h, w = gx.shape
+    _check(library().lbm_nn_avg_pool2_grad(_p(gy), c, d, h, w, _p(gx), _st(stream)), "lbm_nn_avg_pool2_grad")
+
+
+def up2(x, y, stream=None):
+    c, d, h, w = x.shape
+    _check(library().lbm_nn_up2(_p(x), c, d, h, w, _p(y), _st(stream)), "lbm_nn_up2")
+
+
+def up2_grad(gy, gx, stream=None):
+    c, d, h, w = gx.shape
+    _check(library().lbm_nn_up2_grad(_p(gy), c, d, h, w, _p(gx), _st(stream)), "lbm_nn_up2_grad")
+
+
+def rel_loss(p, t, grad, sums, loss=None, stream=None):
+    _check(library().lbm_nn_rel_loss(_p(p), _p(t), p.numel(), _p(grad), _p(sums), _p(loss), _st(stream)),
+           "lbm_nn_rel_loss")
+
+
+def adam(p, g, m, v, lr, b1, b2, eps, step, stream=None):
+    c1, c2 = 1.0 - b1 ** step, 1.0 - b2 ** step
+    _check(library().lbm_nn_adam(_p(p), _p(g), _p(m), _p(v), p.numel(), lr, b1, b2, eps, c1, c2, _st(stream)),
+           "lbm_nn_adam")

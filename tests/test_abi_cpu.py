@@ -17,19 +17,32 @@ def lib():
     return lbm.library()
 
 
-def _declared():
-    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+def _declared(header="lbm.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_exports_every_declared_symbol(lib):
-    from paper_2506_17713_gb300 import lbm
+    from paper_2506_17713_gb300 import lbm, nn
     names = _declared()
     assert len(names) >= 15
     for n in names:
         assert hasattr(lib, n), n
     assert sorted(lbm.EXPORTS) == names
+    nn_names = _declared("lbm_nn.h")
+    assert len(nn_names) == 11
+    for n in nn_names:
+        assert hasattr(lib, n), n
+    assert sorted(nn.EXPORTS) == nn_names
+
+
+def test_network_entry_points_validate_arguments_on_the_host(lib):
+    from paper_2506_17713_gb300 import nn
+    L = nn.library()
+    assert L.lbm_nn_conv3d(None, 1, 4, 4, 4, None, None, 1, 0, None, None) == 1
+    assert L.lbm_nn_avg_pool2(C.c_void_p(256), 1, 3, 4, 4, C.c_void_p(256), None) == 1   # odd size
+    assert L.lbm_nn_adam(None, None, None, None, 0, 0.0, 0.0, 0.0, 0.0, 1.0, 1.0, None) == 1
 
 
 def test_status_strings(lib):

@@ -68,3 +68,10 @@ def test_relative_loss_gradient():
     h = 1e-7
     pp = p.copy(); pp[1, 0, 1, 1] += h
     assert abs((U.rel_loss(pp, t)[0] - L) / h - g[1, 0, 1, 1]) < 1e-5
+
+
+def test_leaky_relu_and_its_gradient():
+    x = np.array([-2.0, -0.5, 0.0, 0.3, 4.0])
+    assert np.allclose(U.relu(x), [-0.02, -0.005, 0.0, 0.3, 4.0])
+    g = np.ones(5)
+    assert np.allclose(U.relu_grad(U.relu(x), g), [0.01, 0.01, 0.01, 1.0, 1.0])
