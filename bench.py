@@ -408,15 +408,16 @@ def run_warmstart(args):
     rows, ideal, pred_err = [], [], []
     for j in range(ntest):
         solid = ws.sample_solid(n, 5000 + j, phis[ntrain + j])
-        sp, tp, kp, _, u_plain = ws.relax(n, solid, None)
+        sp, tp, kp, _, u_plain, rho_plain = ws.relax(n, solid, None)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         pred = ws.predict(net, solid)
         t_inf = time.perf_counter() - t0
-        sw, tw, kw, _, _ = ws.relax(n, solid, pred)
+        sw, tw, kw, _, _, _ = ws.relax(n, solid, pred)
         rows.append((sp, tp, sw, tw + t_inf, kp, kw))
-        # bound on any velocity-only warm start: start from the converged field itself
-        ideal.append(ws.relax(n, solid, u_plain.astype(np.float64))[0])
+        # bounds: start from the converged velocity alone, and from velocity and density
+        ideal.append((ws.relax(n, solid, u_plain.astype(np.float64))[0],
+                      ws.relax(n, solid, u_plain.astype(np.float64), rho0=rho_plain.astype(np.float64))[0]))
         pred_err.append(float(np.linalg.norm(pred - u_plain) / np.linalg.norm(u_plain)))
     r = np.array(rows)
     kerr = np.abs(r[:, 5] - r[:, 4]) / np.abs(r[:, 4])
@@ -435,7 +436,8 @@ def run_warmstart(args):
                    "train_seconds": round(t_train, 1)},
         "steps_to_steady": {"plain_mean": float(r[:, 0].mean()), "warm_mean": float(r[:, 2].mean()),
                             "ratio": round(float(r[:, 0].sum() / r[:, 2].sum()), 3),
-                            "from_converged_velocity_mean": float(np.mean(ideal))},
+                            "from_converged_velocity_mean": float(np.mean([i[0] for i in ideal])),
+                            "from_converged_velocity_and_density_mean": float(np.mean([i[1] for i in ideal]))},
         "prediction_rel_l2_error_mean": round(float(np.mean(pred_err)), 4),
         "wall_seconds": {"plain_total": round(float(r[:, 1].sum()), 3),
                          "warm_total_incl_inference": round(float(r[:, 3].sum()), 3)},

@@ -273,16 +273,17 @@ def predict(net, solid):
     return shape * ritz_scale(shape, solid)
 
 
-def relax(n, solid, u0, check=100, max_steps=60000, tol=1e-6):
+def relax(n, solid, u0, check=100, max_steps=60000, tol=1e-6, rho0=None):
     """steps (multiple of `check`) and wall seconds until the residual is <= tol, from
-    rho = 1 and velocity u0 (None: rest); the permeability nu <u_x> / a, the last
-    residual and the final velocity"""
+    density rho0 (None: 1) and velocity u0 (None: rest); the permeability
+    nu <u_x> / a, the last residual and the final velocity and density"""
     import torch
     lat = Lattice(flow_case(n))
     lat.set_geometry(solid)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    lat.init_fields(0, np.ones((n, n, n)), None if u0 is None else u0.astype(np.float64))
+    rho = np.ones((n, n, n)) if rho0 is None else np.where(solid == 0, rho0, 1.0).astype(np.float64)
+    lat.init_fields(0, rho, None if u0 is None else u0.astype(np.float64))
     lat.diagnostics(residual=True)
     steps = 0
     while steps < max_steps:
@@ -293,7 +294,7 @@ def relax(n, solid, u0, check=100, max_steps=60000, tol=1e-6):
             break
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    _, u = lat.macroscopic_host(0)
+    rho_f, u = lat.macroscopic_host(0)
     k = NU * float(u[0].astype(np.float64).mean()) / ACCEL
     lat.close()
-    return steps, dt, k, r, u
+    return steps, dt, k, r, u, rho_f
