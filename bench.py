@@ -393,12 +393,14 @@ def run_warmstart(args):
     phis = [0.10 + 0.25 * float(v) for v in u]
     t0 = time.perf_counter()
     solids, us, res = [], [], []
-    for b0 in range(0, ntrain, 32):
-        sl = slice(b0, min(ntrain, b0 + 32))
+    for b0 in range(0, ntrain, 64):
+        sl = slice(b0, min(ntrain, b0 + 64))
         so, uu, rr = ws.steady_states(n, list(range(1000 + sl.start, 1000 + sl.stop)), phis[sl], args.ws_steps)
-        solids += so
-        us += uu
-        res += rr
+        for a, b_, c in zip(so, uu, rr):       # train on converged fields only
+            if c <= 1e-5:
+                solids.append(a)
+                us.append(b_)
+                res.append(c)
     t_data = time.perf_counter() - t0
     net = ws.UNet(n, channels=(args.ws_c1, 2 * args.ws_c1, 4 * args.ws_c1), seed=0)
     t0 = time.perf_counter()
@@ -411,9 +413,9 @@ def run_warmstart(args):
         sp, tp, kp, _, u_plain, rho_plain = ws.relax(n, solid, None)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        pred = ws.predict(net, solid)
+        pred, rho_pred = ws.predict(net, solid)
         t_inf = time.perf_counter() - t0
-        sw, tw, kw, _, _, _ = ws.relax(n, solid, pred)
+        sw, tw, kw, _, _, _ = ws.relax(n, solid, pred, rho0=rho_pred)
         rows.append((sp, tp, sw, tw + t_inf, kp, kw))
         # bounds: start from the converged velocity alone, and from velocity and density
         ideal.append((ws.relax(n, solid, u_plain.astype(np.float64))[0],
@@ -432,6 +434,7 @@ def run_warmstart(args):
                    "network": "3-D U-Net, channels %d/%d/%d, %d parameters" % (
                        args.ws_c1, 2 * args.ws_c1, 4 * args.ws_c1, net.parameters()),
                    "epochs": args.ws_epochs, "final_train_loss": round(hist[-1], 4),
+                   "converged_train_samples": len(solids),
                    "train_residual_max": float(max(res)), "data_seconds": round(t_data, 1),
                    "train_seconds": round(t_train, 1)},
         "steps_to_steady": {"plain_mean": float(r[:, 0].mean()), "warm_mean": float(r[:, 2].mean()),
@@ -607,7 +610,8 @@ def main():
     ap.add_argument("--ws-n", type=int, default=48, help="warmstart: sample edge")
     ap.add_argument("--ws-train", type=int, default=96)
     ap.add_argument("--ws-test", type=int, default=16)
-    ap.add_argument("--ws-steps", type=int, default=16000, help="warmstart: steps of the training steady states")
+    ap.add_argument("--ws-steps", type=int, default=40000,
+                    help="warmstart: step limit of the training steady states")
     ap.add_argument("--ws-epochs", type=int, default=40)
     ap.add_argument("--ws-c1", type=int, default=8)
     ap.add_argument("--batch-count", type=int, default=64)

@@ -160,7 +160,10 @@ lbm_status lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void
 lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* solid, int where);
 
 /* Populations of component comp := f^eq(rho, u) at fluid nodes (Eq. macroeq with the
- * second-order equilibrium). rho: [N] doubles; u: [D][N] doubles or NULL for rest. */
+ * second-order equilibrium). rho: [N] doubles; u: [D][N] doubles or NULL for rest.
+ * u is the velocity of the equilibrium populations, i.e. the bare velocity
+ * sum_i f_i e_i / rho; lbm_macroscopic reports (sum_i f_i e_i + F/2) / rho, which is
+ * F/(2 rho) higher. To restart from a reported field, subtract F/(2 rho) first. */
 lbm_status lbm_init_fields(lbm_ctx* ctx, int comp, const double* rho, const double* u,
                            int where);
 

@@ -39,9 +39,11 @@ def sample_solid(n, seed, porosity):
     return solid
 
 
-def steady_states(n, seeds, porosities, steps, stream=None):
-    """Steady velocity fields of the samples, advanced together as one batch for
-    `steps` steps; returns (solids, [3, n, n, n] velocity arrays, residuals)."""
+def steady_states(n, seeds, porosities, steps, stream=None, tol=1e-6, chunk=1000):
+    """Steady fields of the samples, advanced together as one batch in chunks of
+    `chunk` steps until every residual (change over the last chunk) is <= tol or
+    `steps` steps have run; returns (solids, [4, n, n, n] arrays of u_x, u_y, u_z,
+    rho - 1, residuals). The density deviation is formed in FP64 before the FP32 cast."""
     lats, solids = [], []
     for s, phi in zip(seeds, porosities):
         solid = sample_solid(n, s, phi)
@@ -51,16 +53,19 @@ def steady_states(n, seeds, porosities, steps, stream=None):
         lats.append(lat)
         solids.append(solid)
     batch = Batch(lats)
-    batch.step(steps - 100)
     for lat in lats:
         lat.diagnostics(residual=True)
-    batch.step(100)
-    us, res = [], []
+    done, res = 0, [1.0] * len(lats)
+    while done < steps:
+        batch.step(chunk)
+        done += chunk
+        res = [lat.diagnostics(residual=True)[2] for lat in lats]
+        if max(res) <= tol:
+            break
+    us = []
     for lat in lats:
-        _, _, r = lat.diagnostics(residual=True)
-        _, u = lat.macroscopic_host(0)
-        us.append(u.astype(np.float32))
-        res.append(r)
+        rho, u = lat.macroscopic_host(0)
+        us.append(np.concatenate([u, rho[None] - 1.0]).astype(np.float32))
     batch.close()
     for lat in lats:
         lat.close()
@@ -74,16 +79,18 @@ class UNet:
       e2: pool, c1 -> c2 -> c2    (n/2)    skip 2
       b : pool, c2 -> c3 -> c3    (n/4)
       d2: up, [c3 | skip 2] -> c2 -> c2   (n/2)
-      d1: up, [c2 | skip 1] -> c1 -> 3    (n), the last layer linear
+      d1: up, [c2 | skip 1] -> c1 -> 4    (n), the last layer linear
+          (outputs: the flow shape, 3 channels, and the density deviation (rho - 1) / (a n))
 
     Leaky ReLU after every convolution but the last. Parameters and Adam moments are
     FP32; the last layer starts at a tenth of its He initialisation, so the first
     predictions are small and the relative loss starts near 1."""
     CIN = 2
+    COUT = 4
 
     LAYERS = [("e1a", "in", "c1"), ("e1b", "c1", "c1"), ("e2a", "c1", "c2"), ("e2b", "c2", "c2"),
               ("ba", "c2", "c3"), ("bb", "c3", "c3"), ("d2a", "c3+c2", "c2"), ("d2b", "c2", "c2"),
-              ("d1a", "c2+c1", "c1"), ("d1b", "c1", "3")]
+              ("d1a", "c2+c1", "c1"), ("d1b", "c1", "out")]
 
     def __init__(self, n, channels=(8, 16, 32), seed=0):
         import torch
@@ -91,7 +98,7 @@ class UNet:
         self.torch = torch
         self.n = n
         c1, c2, c3 = channels
-        size = {"in": self.CIN, "3": 3, "c1": c1, "c2": c2, "c3": c3, "c3+c2": c3 + c2, "c2+c1": c2 + c1}
+        size = {"in": self.CIN, "out": self.COUT, "c1": c1, "c2": c2, "c3": c3, "c3+c2": c3 + c2, "c2+c1": c2 + c1}
         g = torch.Generator().manual_seed(seed)
         dev = "cuda"
         self.shape = {}
@@ -116,7 +123,7 @@ class UNet:
         # activations (kept for the backward pass); skips written into the concat buffers
         self.a = {"x": e(self.CIN, n), "e1a": e(c1, n), "cat1": e(c2 + c1, n), "p1": e(c1, h), "e2a": e(c2, h),
                   "cat2": e(c3 + c2, h), "p2": e(c2, q), "ba": e(c3, q), "bb": e(c3, q), "d2a": e(c2, h),
-                  "d2b": e(c2, h), "d1a": e(c1, n), "out": e(3, n)}
+                  "d2b": e(c2, h), "d1a": e(c1, n), "out": e(self.COUT, n)}
         self.g = {k: torch.empty_like(v) for k, v in self.a.items()}
         self.g["skip1"] = e(c1, n)
         self.g["skip2"] = e(c2, h)
@@ -134,7 +141,7 @@ class UNet:
         nn.conv3d(x, self.w[name], self.b[name], relu, y)
 
     def forward(self, x):
-        """x: [2, n, n, n] float32 input features (see features()) -> [3, n, n, n]"""
+        """x: [2, n, n, n] float32 input features (see features()) -> [4, n, n, n]"""
         a, (c1, c2, c3) = self.a, self.c
         a["x"].copy_(x)
         skip1 = a["cat1"][c2:]
@@ -216,10 +223,18 @@ def scale_of(u, solid):
     return float((u[0] * (NU / ACCEL))[solid == 0].mean())
 
 
-def targets(us, solids):
-    """network targets: the field nu u / a divided by its velocity scale (unit mean
-    x-velocity over the fluid), so samples of very different permeability weigh alike"""
-    return [(u * (NU / ACCEL) / scale_of(u, s)).astype(np.float32) for u, s in zip(us, solids)]
+def targets(fields, solids):
+    """network targets from steady [u_x, u_y, u_z, rho - 1] fields: the velocity nu u / a
+    divided by its scale (unit mean x-velocity over the fluid), so samples of very
+    different permeability weigh alike, and the density deviation (rho - 1) / (a n),
+    whose size the body force sets (zero in solids)"""
+    out = []
+    for f, s in zip(fields, solids):
+        n = s.shape[0]
+        shape = f[:3] * (NU / ACCEL) / scale_of(f, s)
+        drho = np.where(s == 0, f[3] / (ACCEL * n), 0.0)
+        out.append(np.concatenate([shape, drho[None]]).astype(np.float32))
+    return out
 
 
 def ritz_scale(shape, solid):
@@ -266,11 +281,14 @@ def train(net, solids, us, epochs, batch=8, lr=1e-3, seed=0, log=None):
 
 
 def predict(net, solid):
-    """predicted steady velocity: the network's flow shape at its Ritz scale"""
+    """predicted steady (velocity [3, n, n, n], density [n, n, n]): the network's flow
+    shape at its Ritz scale, and its density deviation"""
     import torch
     x = torch.from_numpy(features(solid)).cuda()
-    shape = net.forward(x).detach().cpu().numpy().astype(np.float64)
-    return shape * ritz_scale(shape, solid)
+    out = net.forward(x).detach().cpu().numpy().astype(np.float64)
+    shape = out[:3]
+    rho = 1.0 + out[3] * ACCEL * solid.shape[0]
+    return shape * ritz_scale(shape, solid), rho
 
 
 def relax(n, solid, u0, check=100, max_steps=60000, tol=1e-6, rho0=None):
@@ -283,7 +301,13 @@ def relax(n, solid, u0, check=100, max_steps=60000, tol=1e-6, rho0=None):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     rho = np.ones((n, n, n)) if rho0 is None else np.where(solid == 0, rho0, 1.0).astype(np.float64)
-    lat.init_fields(0, rho, None if u0 is None else u0.astype(np.float64))
+    ub = None
+    if u0 is not None:
+        # u0 is the reported velocity (sum f e + F/2) / rho; the populations are set at
+        # equilibrium with the bare velocity, half a body-force step lower (Eq. edm)
+        ub = u0.astype(np.float64).copy()
+        ub[0] -= 0.5 * ACCEL * (solid == 0)
+    lat.init_fields(0, rho, ub)
     lat.diagnostics(residual=True)
     steps = 0
     while steps < max_steps:

@@ -149,7 +149,7 @@ def test_unet_forward_and_gradients_against_numpy():
     for k in net.b:                      # nonzero biases exercise the bias gradients
         net.b[k].copy_(_t(_rand(net.b[k].shape[0], 20 + len(k)) * 0.1))
     x = np.random.default_rng(12).random((2, n, n, n))
-    t = _rand((3, n, n, n), 13)
+    t = _rand((4, n, n, n), 13)
     out = net.forward(_t(x))
     loss = float(net.backward(_t(t), accumulate=False).item())
     ref_out, ref_L, G = _ref_unet(net, x, t)
@@ -168,6 +168,6 @@ def test_training_reduces_the_loss():
     rng = np.random.default_rng(5)
     solids = [(rng.random((n, n, n)) > 0.6).astype(np.uint8) for _ in range(4)]
     # targets that a network can fit: a smooth function of the fluid indicator
-    us = [np.stack([(1 - s) * 2e-4, (1 - s) * 1e-5, 0 * s]).astype(np.float32) for s in solids]
+    us = [np.stack([(1 - s) * 2e-4, (1 - s) * 1e-5, 0 * s, 1e-4 * (1 - s)]).astype(np.float32) for s in solids]
     hist = train(net, solids, us, epochs=30, batch=2, lr=3e-3)
     assert hist[-1] < 0.5 * hist[0]

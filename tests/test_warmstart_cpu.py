@@ -30,5 +30,10 @@ def test_features_and_targets():
     assert f.shape == (2, 8, 8, 8)
     assert np.array_equal(f[0], 1.0 - solid)
     assert np.all(f[1][solid == 1] == 0) and abs(f[1][:, 1, :].max() - 1.0 / 8) < 1e-6
-    t = ws.targets([shape.astype(np.float32) * ws.ACCEL / ws.NU], [solid])[0]
+    rho = 1.0 + 2e-4 * np.arange(8)[None, :, None] * np.ones((8, 8, 8))
+    f = np.concatenate([shape * ws.ACCEL / ws.NU, rho[None] - 1.0]).astype(np.float32)
+    t = ws.targets([f], [solid])[0]
+    assert t.shape == (4, 8, 8, 8)
     assert abs(t[0][solid == 0].mean() - 1.0) < 1e-5
+    assert np.allclose(t[3][solid == 0], ((rho - 1) / (ws.ACCEL * 8))[solid == 0], rtol=1e-5)
+    assert np.all(t[3][solid == 1] == 0)
