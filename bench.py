@@ -405,15 +405,16 @@ def run_warmstart(args):
     net = ws.UNet(n, channels=(args.ws_c1, 2 * args.ws_c1, 4 * args.ws_c1), seed=0)
     t0 = time.perf_counter()
     hist = ws.train(net, solids, us, epochs=args.ws_epochs, batch=8)
+    coef = ws.fit_scale(net, solids, us)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    rows, ideal, pred_err = [], [], []
+    rows, ideal, pred_err, scale_err = [], [], [], []
     for j in range(ntest):
         solid = ws.sample_solid(n, 5000 + j, phis[ntrain + j])
         sp, tp, kp, _, u_plain, rho_plain = ws.relax(n, solid, None)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        pred, rho_pred = ws.predict(net, solid)
+        pred, rho_pred = ws.predict(net, solid, coef)
         t_inf = time.perf_counter() - t0
         sw, tw, kw, _, _, _ = ws.relax(n, solid, pred, rho0=rho_pred)
         rows.append((sp, tp, sw, tw + t_inf, kp, kw))
@@ -421,6 +422,7 @@ def run_warmstart(args):
         ideal.append((ws.relax(n, solid, u_plain.astype(np.float64))[0],
                       ws.relax(n, solid, u_plain.astype(np.float64), rho0=rho_plain.astype(np.float64))[0]))
         pred_err.append(float(np.linalg.norm(pred - u_plain) / np.linalg.norm(u_plain)))
+        scale_err.append(ws.scale_of(pred, solid) / ws.scale_of(u_plain, solid))
     r = np.array(rows)
     kerr = np.abs(r[:, 5] - r[:, 4]) / np.abs(r[:, 4])
     if rank != 0:
@@ -442,6 +444,8 @@ def run_warmstart(args):
                             "from_converged_velocity_mean": float(np.mean([i[0] for i in ideal])),
                             "from_converged_velocity_and_density_mean": float(np.mean([i[1] for i in ideal]))},
         "prediction_rel_l2_error_mean": round(float(np.mean(pred_err)), 4),
+        "predicted_over_true_scale": [round(float(v), 3) for v in scale_err],
+        "scale_fit": [round(float(c), 4) for c in coef],
         "wall_seconds": {"plain_total": round(float(r[:, 1].sum()), 3),
                          "warm_total_incl_inference": round(float(r[:, 3].sum()), 3)},
         "permeability": {"max_rel_diff_warm_vs_plain": float(kerr.max()), "plain_mean": float(r[:, 4].mean())},

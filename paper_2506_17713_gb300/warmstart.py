@@ -280,15 +280,40 @@ def train(net, solids, us, epochs, batch=8, lr=1e-3, seed=0, log=None):
     return history
 
 
-def predict(net, solid):
-    """predicted steady (velocity [3, n, n, n], density [n, n, n]): the network's flow
-    shape at its Ritz scale, and its density deviation"""
+def _net_out(net, solid):
     import torch
     x = torch.from_numpy(features(solid)).cuda()
-    out = net.forward(x).detach().cpu().numpy().astype(np.float64)
+    return net.forward(x).detach().cpu().numpy().astype(np.float64)
+
+
+def scale_inputs(solid, shape):
+    """regressors of log(velocity scale): 1, log porosity, log mean squared distance to
+    solid over the fluid, and log of the Ritz scale of the predicted shape"""
+    fl = solid == 0
+    d = features(solid)[1] * 8.0
+    r = ritz_scale(shape, solid) * (NU / ACCEL)
+    return np.array([1.0, np.log(fl.mean()), np.log(np.mean(d[fl] ** 2)), np.log(max(r, 1e-12))])
+
+
+def fit_scale(net, solids, fields):
+    """least-squares fit of log(scale) on scale_inputs over converged training fields"""
+    X = np.array([scale_inputs(s, _net_out(net, s)[:3]) for s in solids])
+    y = np.log([scale_of(f, s) for f, s in zip(fields, solids)])
+    coef, *_ = np.linalg.lstsq(X, y, rcond=None)
+    return coef
+
+
+def predict(net, solid, coef=None):
+    """predicted steady (velocity [3, n, n, n], density [n, n, n]): the network's flow
+    shape at the fitted scale (coef from fit_scale) or else at its Ritz scale, and its
+    density deviation"""
+    out = _net_out(net, solid)
     shape = out[:3]
     rho = 1.0 + out[3] * ACCEL * solid.shape[0]
-    return shape * ritz_scale(shape, solid), rho
+    if coef is None:
+        return shape * ritz_scale(shape, solid), rho
+    scale = float(np.exp(scale_inputs(solid, shape) @ coef)) * (ACCEL / NU)
+    return shape * scale, rho
 
 
 def relax(n, solid, u0, check=100, max_steps=60000, tol=1e-6, rho0=None):
