@@ -1665,7 +1665,7 @@ cudaError_t run_batch_k(int bop, const BatchItem<T>* items, int n_items, const B
 // Launchers
 // ---------------------------------------------------------------------------
 
-inline dim3 node_block(int nx) { return dim3(nx >= 256 ? 256 : ((nx + 31) / 32) * 32, 1, 1); }
+inline dim3 node_block(int nx) { return dim3(nx >= 128 ? 128 : ((nx + 31) / 32) * 32, 1, 1); }
 inline dim3 node_grid(int nx, int ny, int nz, dim3 b) { return dim3((nx + b.x - 1) / b.x, ny, nz); }
 
 template <class L, typename T, typename S, int K, int COLL, bool GEOM>
