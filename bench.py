@@ -33,6 +33,8 @@ WORKLOADS = {
                  "corr. length 6, seed 7), wetting, constant-density x faces",
     "warmstart": "learned warm start of single-phase steady-state runs: D3Q19 BGK, periodic GRF porous "
                  "samples (porosity U[0.1,0.35], corr. length 6), body force; 3-D U-Net trained on LBM steady states",
+    "conv3d": "one periodic 3x3x3 convolution layer of the warm-start U-Net (FP32 activations): forward, "
+              "adjoint and weight gradient, BF16 tensor cores vs FP32 CUDA cores",
     "batch64": "64 D3Q19 sphere-pack drainage samples, box edges U[64,192] (seed 2024), overlapping spheres "
                "r U[8,12] to porosity 0.38, PR T=0.8Tc MRT FP32, wetting solids, per-sample inlet pressure step",
 }
@@ -378,6 +380,68 @@ def run_batch(args):
     batch.close()
 
 
+def run_conv3d(args):
+    """Throughput of the warm-start network's convolution passes on one layer: the
+    tcgen05 implicit GEMMs (BF16 operands, FP32 accumulation) against the FP32
+    CUDA-core kernels, 2 * 27 * cin * cout flops per voxel and pass, CUDA events over
+    --steps repetitions of each pass after --warmup."""
+    import torch
+    from paper_2506_17713_gb300 import nn
+    torch.cuda.set_device(0)
+    cin, cout, n = args.conv_cin, args.conv_cout, args.conv_n
+    g = torch.Generator(device="cuda").manual_seed(7)
+    x = torch.randn(cin, n, n, n, device="cuda", generator=g)
+    gy = torch.randn(cout, n, n, n, device="cuda", generator=g)
+    w = torch.randn(cout, cin, 27, device="cuda", generator=g) * (2.0 / (27 * cin)) ** 0.5
+    b = torch.randn(cout, device="cuda", generator=g)
+    y = torch.empty(cout, n, n, n, device="cuda")
+    gx = torch.empty(cin, n, n, n, device="cuda")
+    wt = torch.empty(cin * cout * 27, device="cuda")
+    gw = torch.empty(cout, cin, 27, device="cuda")
+    gb = torch.empty(cout, device="cuda")
+    sc = torch.empty(max(nn.gw_scratch_floats(cin, cout, True), nn.gw_scratch_floats(cin, cout, False)),
+                     device="cuda")
+    flops = 2.0 * 27 * cin * cout * n ** 3
+    passes = {"forward": lambda tc: nn.conv3d(x, w, b, True, y, tc=tc),
+              "grad_input": lambda tc: nn.conv3d_grad_input(gy, w, wt, gx, tc=tc),
+              "grad_weight": lambda tc: nn.conv3d_grad_weight(x, gy, gw, gb, False, sc, tc=tc)}
+    res = {}
+    clk_sampler = ClockSampler(0)
+    clk_sampler.start()
+    for tc in (True, False):
+        for name, fn in passes.items():
+            for _ in range(args.warmup):
+                fn(tc)
+            torch.cuda.synchronize()
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(args.steps):
+                fn(tc)
+            e.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(e) / args.steps
+            res[("tc_" if tc else "fp32_") + name] = {"ms": round(ms, 4), "tflops": round(flops / ms / 1e9, 2)}
+    clk = clk_sampler.stop()
+    if nn.tc_error():
+        raise RuntimeError("a tensor-core wait gave up")
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+        peak = float(json.load(fh)["bf16_tflops"])
+    fwd = res["tc_forward"]
+    launches = 3 * (args.steps + args.warmup) + 2 * 2 * (args.steps + args.warmup)   # tc: 1 + 2 + 2 per rep
+    print(json.dumps({
+        "metric": "conv3d forward TFLOP/s (BF16 tensor cores)", "value": fwd["tflops"], "unit": "TFLOP/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": fwd["ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": WORKLOADS["conv3d"], "cin": cin, "cout": cout, "edge": n,
+                   "l2": "input %.0f MB and output %.0f MB per pass against a 129 MB L2" % (
+                       cin * n ** 3 * 4 / 1e6, cout * n ** 3 * 4 / 1e6)},
+        "passes": res,
+        "roofline": {"bound": "tensor", "kernel": "k_conv3d_tc", "achieved": fwd["tflops"], "peak": peak,
+                     "unit": "TFLOP/s", "frac": round(fwd["tflops"] / peak, 4), "peak_kind": "measured bf16 burst",
+                     "traffic": None},
+        "gpu_launches": launches, "clocks": clk}))
+
+
 def run_warmstart(args):
     """Time to steady state (residual <= 1e-6) of held-out samples, from the network's
     prediction vs from rest; the network is trained in the same run on steady states
@@ -402,7 +466,8 @@ def run_warmstart(args):
                 us.append(b_)
                 res.append(c)
     t_data = time.perf_counter() - t0
-    net = ws.UNet(n, channels=(args.ws_c1, 2 * args.ws_c1, 4 * args.ws_c1), seed=0)
+    net = ws.UNet(n, channels=(args.ws_c1, 2 * args.ws_c1, 4 * args.ws_c1), seed=0,
+                  tensor_cores=not args.ws_fp32)
     t0 = time.perf_counter()
     hist = ws.train(net, solids, us, epochs=args.ws_epochs, batch=8)
     coef = ws.fit_scale(net, solids, us)
@@ -433,8 +498,10 @@ def run_warmstart(args):
         "steps": int(r[:, 2].sum()), "warmup": 0, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS["warmstart"], "edge": n, "train_samples": ntrain, "test_samples": ntest,
-                   "network": "3-D U-Net, channels %d/%d/%d, %d parameters" % (
-                       args.ws_c1, 2 * args.ws_c1, 4 * args.ws_c1, net.parameters()),
+                   "network": "3-D U-Net, channels %d/%d/%d, %d parameters, %s" % (
+                       args.ws_c1, 2 * args.ws_c1, 4 * args.ws_c1, net.parameters(),
+                       "FP32 CUDA-core convolutions" if args.ws_fp32
+                       else "BF16 tensor-core convolutions (FP32 accumulation)"),
                    "epochs": args.ws_epochs, "final_train_loss": round(hist[-1], 4),
                    "converged_train_samples": len(solids),
                    "train_residual_max": float(max(res)), "data_seconds": round(t_data, 1),
@@ -618,6 +685,10 @@ def main():
                     help="warmstart: step limit of the training steady states")
     ap.add_argument("--ws-epochs", type=int, default=40)
     ap.add_argument("--ws-c1", type=int, default=8)
+    ap.add_argument("--ws-fp32", action="store_true", help="warm-start network on FP32 CUDA cores")
+    ap.add_argument("--conv-cin", type=int, default=32, help="conv3d: input channels")
+    ap.add_argument("--conv-cout", type=int, default=32, help="conv3d: output channels")
+    ap.add_argument("--conv-n", type=int, default=128, help="conv3d: cube edge")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-edge-lo", type=int, default=64)
     ap.add_argument("--batch-edge-hi", type=int, default=192)
@@ -632,6 +703,8 @@ def main():
         run_batch(args)
     elif args.workload == "warmstart":
         run_warmstart(args)
+    elif args.workload == "conv3d":
+        run_conv3d(args)
     else:
         run_ours(args)
 

@@ -68,6 +68,34 @@ lbm_status lbm_nn_rel_loss(const float* p, const float* t, long long n, float* g
 lbm_status lbm_nn_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2,
                        float eps, float c1, float c2, void* stream);
 
+/*
+ * The three convolution passes on the tcgen05 tensor cores (same arguments and layouts
+ * as the FP32 entry points above; the weight gradient splits the voxels into up to
+ * LBM_NN_GW_TC_SEGMENTS segments and takes scratch of LBM_NN_GW_TC_SEGMENTS * cout *
+ * (27 cin + 1) floats). Each is an implicit GEMM with M = 128
+ * voxels (forward, adjoint) or 128 (tap, channel) rows (weight gradient), N = output
+ * channels rounded up to 16, and BF16 operands: x, the weights and gy are rounded from
+ * FP32 to BF16 (to nearest, ties to even) as they are staged in shared memory, and the
+ * products are accumulated in FP32 in tensor memory. Bias, leaky ReLU and the segment
+ * sums stay FP32. Limits (LBM_ERR_INVALID_ARG beyond them): d h w < 2^31 - 128 voxels,
+ * cout <= 256, and the forward pass needs 54 Np Cp + 512 Cp + 2048 bytes of shared
+ * memory <= 227 KB, with Np = cout and Cp = cin rounded up to 16 (for the adjoint, cout
+ * and cin swap roles).
+ * A wait on the tensor cores that does not end within about 2 s makes the kernel stop,
+ * free its tensor memory and set a flag that lbm_nn_tc_error reads.
+ */
+#define LBM_NN_GW_TC_SEGMENTS 512
+lbm_status lbm_nn_conv3d_tc(const float* x, int cin, int d, int h, int w, const float* weight,
+                            const float* bias, int cout, int relu, float* y, void* stream);
+lbm_status lbm_nn_conv3d_tc_grad_input(const float* gy, int cout, int d, int h, int w, const float* weight,
+                                       int cin, float* wt_scratch, float* gx, void* stream);
+lbm_status lbm_nn_conv3d_tc_grad_weight(const float* x, int cin, const float* gy, int cout, int d, int h, int w,
+                                        float* gw, float* gb, int accumulate, float* scratch, void* stream);
+
+/* *flag = 1 if a tensor-core wait gave up since the last call, else 0; clears the flag.
+ * Synchronises the device. */
+lbm_status lbm_nn_tc_error(int* flag);
+
 #ifdef __cplusplus
 }
 #endif

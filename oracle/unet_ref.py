@@ -10,7 +10,9 @@ periodic), so a 3x3x3 convolution wraps around instead of padding with zeros:
 
 avg_pool2 averages 2x2x2 blocks; up2 repeats each voxel into a 2x2x2 block; relu is
 the leaky ReLU (slope 0.01 below zero); the loss is the relative squared error
-sum (p - t)^2 / sum t^2.
+sum (p - t)^2 / sum t^2. bf16 rounds FP32 values to bfloat16 (8 significant bits, the
+FP32 exponent range), to nearest with ties to even: the operand rounding of the
+tensor-core convolutions.
 """
 import numpy as np
 
@@ -20,6 +22,18 @@ OFFS = [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0,
 def shift(x, dz, dy, dx):
     """x[(z+dz), (y+dy), (x+dx)] on the periodic box (last three axes)"""
     return np.roll(x, (-dz, -dy, -dx), axis=(-3, -2, -1))
+
+
+def bf16(a):
+    """a (any float array, taken as FP32) rounded to the nearest bfloat16, ties to even,
+    returned as float64. Finite values only."""
+    f = np.ascontiguousarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    keep = u >> 16                      # sign, exponent and the 7 stored fraction bits
+    rest = u & 0xFFFF                   # the 16 dropped bits
+    up = (rest > 0x8000) | ((rest == 0x8000) & (keep & 1 == 1))
+    out = ((keep + up) << 16).astype(np.uint32)
+    return out.view(np.float32).astype(np.float64).reshape(f.shape)
 
 
 def conv3d(x, w, b):

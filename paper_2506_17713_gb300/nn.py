@@ -7,8 +7,14 @@ from .lbm import LbmError, library as _lbm_library
 
 EXPORTS = ["lbm_nn_conv3d", "lbm_nn_conv3d_grad_input", "lbm_nn_conv3d_grad_weight", "lbm_nn_axpy", "lbm_nn_relu_grad",
            "lbm_nn_avg_pool2", "lbm_nn_avg_pool2_grad", "lbm_nn_up2", "lbm_nn_up2_grad", "lbm_nn_rel_loss",
-           "lbm_nn_adam"]
-GW_SEGMENTS = 64
+           "lbm_nn_adam", "lbm_nn_conv3d_tc", "lbm_nn_conv3d_tc_grad_input", "lbm_nn_conv3d_tc_grad_weight",
+           "lbm_nn_tc_error"]
+GW_SEGMENTS = 64          # LBM_NN_GW_SEGMENTS: scratch of conv3d_grad_weight, 64 cout cin 28 floats
+GW_TC_SEGMENTS = 512      # LBM_NN_GW_TC_SEGMENTS: scratch of the tensor-core form, 512 cout (27 cin + 1) floats
+
+
+def gw_scratch_floats(cin, cout, tc=False):
+    return GW_TC_SEGMENTS * cout * (27 * cin + 1) if tc else GW_SEGMENTS * cout * cin * 28
 
 _ready = False
 
@@ -29,6 +35,10 @@ def library():
         L.lbm_nn_up2_grad.argtypes = [vp, i, i, i, i, vp, vp]
         L.lbm_nn_rel_loss.argtypes = [vp, vp, ll, vp, vp, vp, vp]
         L.lbm_nn_adam.argtypes = [vp, vp, vp, vp, ll, f, f, f, f, f, f, vp]
+        L.lbm_nn_conv3d_tc.argtypes = L.lbm_nn_conv3d.argtypes
+        L.lbm_nn_conv3d_tc_grad_input.argtypes = L.lbm_nn_conv3d_grad_input.argtypes
+        L.lbm_nn_conv3d_tc_grad_weight.argtypes = L.lbm_nn_conv3d_grad_weight.argtypes
+        L.lbm_nn_tc_error.argtypes = [C.POINTER(C.c_int)]
         for n in EXPORTS:
             getattr(L, n).restype = C.c_int
         _ready = True
@@ -49,23 +59,35 @@ def _check(s, where):
         raise LbmError(s, where)
 
 
-def conv3d(x, w, b, relu, y, stream=None):
+def _name(base, tc):
+    return base.replace("lbm_nn_conv3d", "lbm_nn_conv3d_tc") if tc else base
+
+
+def conv3d(x, w, b, relu, y, stream=None, tc=False):
+    """tc: BF16 operands on the tensor cores (lbm_nn_conv3d_tc), else FP32 CUDA cores"""
     cin, d, h, wd = x.shape
-    _check(library().lbm_nn_conv3d(_p(x), cin, d, h, wd, _p(w), _p(b), w.shape[0], int(relu), _p(y), _st(stream)),
-           "lbm_nn_conv3d")
+    n = _name("lbm_nn_conv3d", tc)
+    _check(getattr(library(), n)(_p(x), cin, d, h, wd, _p(w), _p(b), w.shape[0], int(relu), _p(y), _st(stream)), n)
 
 
-def conv3d_grad_input(gy, w, wt_scratch, gx, stream=None):
+def conv3d_grad_input(gy, w, wt_scratch, gx, stream=None, tc=False):
     cout, d, h, wd = gy.shape
-    _check(library().lbm_nn_conv3d_grad_input(_p(gy), cout, d, h, wd, _p(w), w.shape[1], _p(wt_scratch), _p(gx),
-                                              _st(stream)), "lbm_nn_conv3d_grad_input")
+    n = _name("lbm_nn_conv3d_grad_input", tc)
+    _check(getattr(library(), n)(_p(gy), cout, d, h, wd, _p(w), w.shape[1], _p(wt_scratch), _p(gx), _st(stream)), n)
 
 
-def conv3d_grad_weight(x, gy, gw, gb, accumulate, scratch, stream=None):
+def conv3d_grad_weight(x, gy, gw, gb, accumulate, scratch, stream=None, tc=False):
     cin, d, h, wd = x.shape
-    _check(library().lbm_nn_conv3d_grad_weight(_p(x), cin, _p(gy), gy.shape[0], d, h, wd, _p(gw), _p(gb),
-                                               int(accumulate), _p(scratch), _st(stream)),
-           "lbm_nn_conv3d_grad_weight")
+    n = _name("lbm_nn_conv3d_grad_weight", tc)
+    _check(getattr(library(), n)(_p(x), cin, _p(gy), gy.shape[0], d, h, wd, _p(gw), _p(gb), int(accumulate),
+                                 _p(scratch), _st(stream)), n)
+
+
+def tc_error():
+    """1 if a tensor-core kernel gave up waiting since the last call (clears the flag)"""
+    flag = C.c_int(0)
+    _check(library().lbm_nn_tc_error(C.byref(flag)), "lbm_nn_tc_error")
+    return flag.value
 
 
 def axpy(y, x, a=1.0, stream=None):

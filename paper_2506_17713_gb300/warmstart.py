@@ -84,7 +84,9 @@ class UNet:
 
     Leaky ReLU after every convolution but the last. Parameters and Adam moments are
     FP32; the last layer starts at a tenth of its He initialisation, so the first
-    predictions are small and the relative loss starts near 1."""
+    predictions are small and the relative loss starts near 1. With tensor_cores (the
+    default) the convolutions and their gradients run as BF16 implicit GEMMs on the
+    tensor cores with FP32 accumulation; otherwise in FP32 on the CUDA cores."""
     CIN = 2
     COUT = 4
 
@@ -92,11 +94,12 @@ class UNet:
               ("ba", "c2", "c3"), ("bb", "c3", "c3"), ("d2a", "c3+c2", "c2"), ("d2b", "c2", "c2"),
               ("d1a", "c2+c1", "c1"), ("d1b", "c1", "out")]
 
-    def __init__(self, n, channels=(8, 16, 32), seed=0):
+    def __init__(self, n, channels=(8, 16, 32), seed=0, tensor_cores=True):
         import torch
         assert n % 4 == 0
         self.torch = torch
         self.n = n
+        self.tc = bool(tensor_cores)
         c1, c2, c3 = channels
         size = {"in": self.CIN, "out": self.COUT, "c1": c1, "c2": c2, "c3": c3, "c3+c2": c3 + c2, "c2+c1": c2 + c1}
         g = torch.Generator().manual_seed(seed)
@@ -129,7 +132,8 @@ class UNet:
         self.g["skip2"] = e(c2, h)
         maxw = max(ci * co for ci, co in self.shape.values())
         self.wt = torch.empty(maxw * 27, device=dev)
-        self.gw_scratch = torch.empty(nn.GW_SEGMENTS * maxw * 28, device=dev)
+        self.gw_scratch = torch.empty(max(nn.gw_scratch_floats(ci, co, self.tc) for ci, co in self.shape.values()),
+                                      device=dev)
         self.sums = torch.zeros(2, dtype=torch.float64, device=dev)
         self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
         self.c = (c1, c2, c3)
@@ -138,7 +142,7 @@ class UNet:
         return sum(self.w[k].numel() + self.b[k].numel() for k in self.w)
 
     def _conv(self, name, x, y, relu):
-        nn.conv3d(x, self.w[name], self.b[name], relu, y)
+        nn.conv3d(x, self.w[name], self.b[name], relu, y, tc=self.tc)
 
     def forward(self, x):
         """x: [2, n, n, n] float32 input features (see features()) -> [4, n, n, n]"""
@@ -167,9 +171,9 @@ class UNet:
         if relu:
             nn.relu_grad(y_post, gy)
         cin, cout = self.shape[name]
-        nn.conv3d_grad_weight(x, gy, self.gw[name], self.gb[name], accumulate, self.gw_scratch)
+        nn.conv3d_grad_weight(x, gy, self.gw[name], self.gb[name], accumulate, self.gw_scratch, tc=self.tc)
         if gx is not None:
-            nn.conv3d_grad_input(gy, self.w[name], self.wt[: cin * cout * 27], gx)
+            nn.conv3d_grad_input(gy, self.w[name], self.wt[: cin * cout * 27], gx, tc=self.tc)
 
     def backward(self, target, accumulate):
         """loss = sum (out - target)^2 / sum target^2; accumulate adds to the stored

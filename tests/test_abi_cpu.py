@@ -31,7 +31,7 @@ def test_exports_every_declared_symbol(lib):
         assert hasattr(lib, n), n
     assert sorted(lbm.EXPORTS) == names
     nn_names = _declared("lbm_nn.h")
-    assert len(nn_names) == 11
+    assert len(nn_names) == 15
     for n in nn_names:
         assert hasattr(lib, n), n
     assert sorted(nn.EXPORTS) == nn_names
@@ -43,6 +43,14 @@ def test_network_entry_points_validate_arguments_on_the_host(lib):
     assert L.lbm_nn_conv3d(None, 1, 4, 4, 4, None, None, 1, 0, None, None) == 1
     assert L.lbm_nn_avg_pool2(C.c_void_p(256), 1, 3, 4, 4, C.c_void_p(256), None) == 1   # odd size
     assert L.lbm_nn_adam(None, None, None, None, 0, 0.0, 0.0, 0.0, 0.0, 1.0, 1.0, None) == 1
+    # tensor-core forms: null pointers, more than 256 output channels, shared memory beyond 227 KB
+    fake = C.c_void_p(256)
+    assert L.lbm_nn_conv3d_tc(None, 1, 4, 4, 4, fake, None, 1, 0, fake, None) == 1
+    assert L.lbm_nn_conv3d_tc(fake, 1, 4, 4, 4, fake, None, 300, 0, fake, None) == 1
+    assert L.lbm_nn_conv3d_tc(fake, 256, 4, 4, 4, fake, None, 256, 0, fake, None) == 1
+    assert L.lbm_nn_conv3d_tc_grad_input(fake, 300, 4, 4, 4, fake, 8, fake, fake, None) == 1
+    assert L.lbm_nn_conv3d_tc_grad_weight(fake, 8, fake, 300, 4, 4, 4, fake, None, 0, fake, None) == 1
+    assert L.lbm_nn_tc_error(None) == 1
 
 
 def test_status_strings(lib):

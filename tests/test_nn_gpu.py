@@ -1,6 +1,12 @@
 """Warm-start network kernels (include/lbm_nn.h) against the numpy reference
 (oracle/unet_ref.py), and the U-Net's gradients against a numpy backward pass
-composed from the same reference operations."""
+composed from the same reference operations.
+
+The tensor-core convolutions take BF16 operands and accumulate in FP32, so they are
+compared with the FP64 convolution of the BF16-rounded operands (unet_ref.bf16) under
+the standard bound for a sum of K exact products accumulated in FP32,
+|err| <= gamma_K sum |a_k b_k|, gamma_K = K u / (1 - K u), u = 2^-24, taken twice
+over (the tensor cores' internal adder order and rounding are not specified)."""
 import numpy as np
 import pytest
 
@@ -142,10 +148,117 @@ def _ref_unet(net, x, t):
     return out, L, G
 
 
+def _gamma(k):
+    u = 2.0 ** -24
+    return 2 * k * u / (1 - k * u)
+
+
+def _within(got, ref, mag, k):
+    err = np.abs(got - ref)
+    bound = _gamma(k) * mag + 2.0 ** -23 * np.abs(ref) + 1e-30
+    assert np.all(err <= bound), (float((err / bound).max()), float(err.max()))
+
+
+# several 128-voxel tiles with a ragged tail; channel counts below, at and above 16;
+# the last case has more tiles than resident CTAs, so CTAs loop over tiles
+TC_CASES = [(5, 11, (6, 4, 10)), (2, 8, (8, 8, 8)), (48, 16, (6, 8, 12)), (16, 32, (4, 4, 8)),
+            (24, 4, (12, 12, 12)), (33, 40, (5, 7, 9)), (2, 8, (64, 72, 72))]
+
+
+@pytest.mark.parametrize("cin,cout,dims", TC_CASES)
+def test_tensor_core_conv3d_forward(cin, cout, dims):
+    import torch
+    from paper_2506_17713_gb300 import nn
+    x = _rand((cin,) + dims, 1)
+    w = _rand((cout, cin, 3, 3, 3), 2) * 0.3
+    b = _rand(cout, 3)
+    xb, wb = U.bf16(x), U.bf16(w)
+    ref = U.conv3d(xb, wb, b)
+    mag = U.conv3d(np.abs(xb), np.abs(wb), np.abs(b))
+    y = torch.empty((cout,) + dims, device="cuda")
+    nn.conv3d(_t(x), _t(w.reshape(cout, cin, 27)), _t(b), False, y, tc=True)
+    _within(_n(y), ref, mag, 27 * cin + 1)
+    yr = torch.empty_like(y)
+    nn.conv3d(_t(x), _t(w.reshape(cout, cin, 27)), _t(b), True, yr, tc=True)
+    assert np.allclose(_n(yr), U.relu(_n(y)), rtol=1e-6, atol=0)
+    nn.conv3d(_t(x), _t(w.reshape(cout, cin, 27)), None, False, y, tc=True)      # no bias
+    _within(_n(y), ref - b[:, None, None, None], mag, 27 * cin + 1)
+    assert nn.tc_error() == 0
+
+
+@pytest.mark.parametrize("cin,cout,dims", TC_CASES[:-1])
+def test_tensor_core_conv3d_gradients(cin, cout, dims):
+    import torch
+    from paper_2506_17713_gb300 import nn
+    x = _rand((cin,) + dims, 5)
+    w = _rand((cout, cin, 3, 3, 3), 6) * 0.3
+    gy = _rand((cout,) + dims, 7)
+    xb, wb, gyb = U.bf16(x), U.bf16(w), U.bf16(gy)
+    gx_ref, _, _ = U.conv3d_grads(xb, wb, gyb)
+    gx_mag, _, _ = U.conv3d_grads(np.abs(xb), np.abs(wb), np.abs(gyb))
+    gx = torch.empty((cin,) + dims, device="cuda")
+    nn.conv3d_grad_input(_t(gy), _t(w.reshape(cout, cin, 27)), torch.empty(cin * cout * 27, device="cuda"), gx,
+                         tc=True)
+    _within(_n(gx), gx_ref, gx_mag, 27 * cout)
+    _, gw_ref, gb_ref = U.conv3d_grads(xb, w, gyb)
+    _, gw_mag, gb_mag = U.conv3d_grads(np.abs(xb), w, np.abs(gyb))
+    P = int(np.prod(dims))
+    gw = torch.empty(cout, cin, 27, device="cuda")
+    gb = torch.empty(cout, device="cuda")
+    scratch = torch.empty(nn.gw_scratch_floats(cin, cout, tc=True), device="cuda")
+    nn.conv3d_grad_weight(_t(x), _t(gy), gw, gb, False, scratch, tc=True)
+    _within(_n(gw), gw_ref.reshape(cout, cin, 27), gw_mag.reshape(cout, cin, 27), P)
+    _within(_n(gb), gb_ref, gb_mag, P)
+    nn.conv3d_grad_weight(_t(x), _t(gy), gw, gb, True, scratch, tc=True)        # accumulate: twice the sum
+    _within(_n(gw), 2 * gw_ref.reshape(cout, cin, 27), 2 * gw_mag.reshape(cout, cin, 27), P + 1)
+    assert nn.tc_error() == 0
+
+
+def test_tensor_core_weight_gradient_over_many_row_tiles():
+    # 27 cin + 1 = 2593 rows: 21 row tiles of 128, the last one ragged
+    import torch
+    from paper_2506_17713_gb300 import nn
+    cin, cout, dims = 96, 32, (4, 6, 8)
+    x = _rand((cin,) + dims, 8)
+    gy = _rand((cout,) + dims, 9)
+    xb, gyb = U.bf16(x), U.bf16(gy)
+    w0 = np.zeros((cout, cin, 3, 3, 3))
+    _, gw_ref, gb_ref = U.conv3d_grads(xb, w0, gyb)
+    _, gw_mag, gb_mag = U.conv3d_grads(np.abs(xb), w0, np.abs(gyb))
+    gw = torch.empty(cout, cin, 27, device="cuda")
+    gb = torch.empty(cout, device="cuda")
+    scratch = torch.empty(nn.gw_scratch_floats(cin, cout, tc=True), device="cuda")
+    nn.conv3d_grad_weight(_t(x), _t(gy), gw, gb, False, scratch, tc=True)
+    P = int(np.prod(dims))
+    _within(_n(gw), gw_ref.reshape(cout, cin, 27), gw_mag.reshape(cout, cin, 27), P)
+    _within(_n(gb), gb_ref, gb_mag, P)
+    assert nn.tc_error() == 0
+
+
+def test_unet_on_tensor_cores_against_numpy():
+    # BF16 operands in ten layers: the output and every gradient within a few per cent
+    # of the FP64 network with the same weights
+    from paper_2506_17713_gb300.warmstart import UNet
+    n = 8
+    net = UNet(n, channels=(4, 6, 8), seed=3, tensor_cores=True)
+    for k in net.b:
+        net.b[k].copy_(_t(_rand(net.b[k].shape[0], 20 + len(k)) * 0.1))
+    x = np.random.default_rng(12).random((2, n, n, n))
+    t = _rand((4, n, n, n), 13)
+    out = net.forward(_t(x))
+    loss = float(net.backward(_t(t), accumulate=False).item())
+    ref_out, ref_L, G = _ref_unet(net, x, t)
+    _close(_n(out), ref_out, 3e-2)
+    assert abs(loss - ref_L) < 3e-2 * ref_L
+    for k, (gw, gb) in G.items():
+        _close(_n(net.gw[k]), gw, 6e-2)
+        _close(_n(net.gb[k]), gb, 6e-2)
+
+
 def test_unet_forward_and_gradients_against_numpy():
     from paper_2506_17713_gb300.warmstart import UNet
     n = 8
-    net = UNet(n, channels=(4, 6, 8), seed=3)
+    net = UNet(n, channels=(4, 6, 8), seed=3, tensor_cores=False)
     for k in net.b:                      # nonzero biases exercise the bias gradients
         net.b[k].copy_(_t(_rand(net.b[k].shape[0], 20 + len(k)) * 0.1))
     x = np.random.default_rng(12).random((2, n, n, n))

@@ -75,3 +75,28 @@ def test_leaky_relu_and_its_gradient():
     assert np.allclose(U.relu(x), [-0.02, -0.005, 0.0, 0.3, 4.0])
     g = np.ones(5)
     assert np.allclose(U.relu_grad(U.relu(x), g), [0.01, 0.01, 0.01, 1.0, 1.0])
+
+
+def test_bf16_rounding_against_exact_cases():
+    # bfloat16 keeps 8 significant bits: spacing 2^-7 on [1, 2)
+    u = 2.0 ** -7
+    cases = [(1.0, 1.0), (1.0 + u, 1.0 + u), (1.0 + u / 2, 1.0),          # tie -> even (1.0)
+             (1.0 + 3 * u / 2, 1.0 + 2 * u),                                  # tie -> even (1 + 2u)
+             (1.0 + u / 2 + 2.0 ** -20, 1.0 + u),                             # above the tie
+             (1.0 + u / 2 - 2.0 ** -20, 1.0),                                 # below the tie
+             (-3.0 - 0.75 * 2 * u, -3.0 - 2 * u),                             # spacing 2u on [2, 4)
+             (2.0 - u / 4, 2.0),                                              # carries into the exponent
+             (0.0, 0.0), (2.0 ** -130, 2.0 ** -130)]                          # zero, subnormal kept exactly
+    for v, r in cases:
+        assert U.bf16(np.array([v]))[0] == r, (v, U.bf16(np.array([v]))[0], r)
+
+
+def test_bf16_rounding_error_bound_and_idempotence():
+    x = _rand(10000, 30) * 10.0 ** np.random.default_rng(31).integers(-6, 6, 10000)
+    r = U.bf16(x)
+    xf = x.astype(np.float32).astype(np.float64)
+    assert np.all(np.abs(r - xf) <= 2.0 ** -8 * np.abs(xf))      # unit roundoff of 8 significant bits
+    assert np.array_equal(U.bf16(r), r)
+    # every result has at most 8 significant bits
+    m, _ = np.frexp(r[r != 0])
+    assert np.array_equal(m * 2 ** 8, np.round(m * 2 ** 8))
