@@ -413,8 +413,8 @@ struct TcConv {
 // Implicit GEMM with rows = 128 voxels, K = (tap, channel) with channel fastest, N = o.
 // Shared memory: [barriers | B = weights, whole K | A stage 0 | A stage 1]; a stage holds
 // s.taps taps of 128 x cp BF16. Thread m builds row m; CP16 = cp / 16 when fixed at
-// compile time (0: read from s).
-template <int CP16>
+// compile time (0: read from s); FULL: cin = cp, no padded channels to zero.
+template <int CP16, bool FULL>
 __global__ void __launch_bounds__(kRows, 1) k_conv3d_tc(const float* __restrict__ x, const float* __restrict__ wt,
                                                         const float* __restrict__ bias, TcConv s, int relu,
                                                         float* __restrict__ y)
@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(kRows, 1) k_conv3d_tc(const float* __restrict_
                     float v[8];
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
-                        v[e] = c * 8 + e < s.cin ? *src : 0.0f;
+                        v[e] = FULL || c * 8 + e < s.cin ? *src : 0.0f;
                         src += P;
                     }
                     store_row8(row + c * 128, v);
@@ -559,9 +559,12 @@ __global__ void __launch_bounds__(kRows) k_conv3d_gw_tc(const float* __restrict_
     uint8_t* bst0 = smem + 1024 + 2 * kTab * 4;               // stage k at bst0 + k * b_bytes
     uint8_t* ast0 = bst0 + 2 * b_bytes;                       // stage k at ast0 + k * a_bytes
     const int m = threadIdx.x, warp = m >> 5;
-    const int seg = blockIdx.x, r = blockIdx.y * kRows + m;
+    const int seg = blockIdx.x, r0 = blockIdx.y * kRows, r = r0 + m;
     const bool wrow = r < 27 * s.cin, ones = r == 27 * s.cin;
-    const int t = wrow ? r / s.cin : 0;
+    // taps met by the weight rows of this tile: the neighbour table holds only these
+    const int t_lo = r0 / s.cin, t_hi = (r0 + kRows - 1) / s.cin < 26 ? (r0 + kRows - 1) / s.cin : 26;
+    const int ntab = t_lo <= t_hi ? (t_hi - t_lo + 1) * kGwK : 0;
+    const int t = wrow ? r / s.cin : t_lo;
     const float* xi = x + (size_t)(wrow ? r % s.cin : 0) * s.P;
     if (m == 0) {
         mbar_init(smem_addr(&bars[0]));
@@ -590,8 +593,8 @@ __global__ void __launch_bounds__(kRows) k_conv3d_gw_tc(const float* __restrict_
         int* nbr = nbr0 + st * kTab;
         uint8_t* bst = bst0 + st * b_bytes;
         uint8_t* ast = ast0 + st * a_bytes;
-        for (int e = m; e < kTab; e += kRows) {               // neighbour of voxel p0 + k at tap tt, or -1
-            const int k = e % kGwK, tt = e / kGwK, p = p0 + k;
+        for (int e = m; e < ntab; e += kRows) {               // neighbour of voxel p0 + k at tap tt, or -1
+            const int k = e % kGwK, tt = t_lo + e / kGwK, p = p0 + k;
             nbr[e] = p < s.P ? tap_index(voxel(p, s.H, s.W), tt, s.D, s.H, s.W) : -1;
         }
         for (int e = m; e < s.npad * (kGwK / 8); e += kRows) {  // B: gy rows, 8 voxels per core-matrix row
@@ -606,15 +609,20 @@ __global__ void __launch_bounds__(kRows) k_conv3d_gw_tc(const float* __restrict_
         }
         __syncthreads();
         {                                                      // A: this thread's row
-            const int* nt = nbr + t * kGwK;
+            const int* nt = nbr + (wrow ? (t - t_lo) * kGwK : 0);
             uint8_t* row = ast + (m / 8) * (kGwK * 16) + (m % 8) * 16;
 #pragma unroll
             for (int h = 0; h < kGwK / 8; ++h) {
                 float v[8];
+                if (wrow) {
+                    const int4 a = *reinterpret_cast<const int4*>(nt + h * 8);
+                    const int4 b = *reinterpret_cast<const int4*>(nt + h * 8 + 4);
+                    const int nq[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int nq = nt[h * 8 + q];
-                    v[q] = wrow ? (nq >= 0 ? xi[nq] : 0.0f) : (ones && nq >= 0 ? 1.0f : 0.0f);
+                    for (int q = 0; q < 8; ++q) v[q] = nq[q] >= 0 ? xi[nq[q]] : 0.0f;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) v[q] = ones && p0 + h * 8 + q < s.P ? 1.0f : 0.0f;
                 }
                 store_row8(row + h * 128, v);
             }
@@ -748,29 +756,35 @@ lbm_status conv_tc_shape(int cin, int d, int h, int w, int cout, TcConv& s, size
     return bytes > kMaxSmem ? LBM_ERR_INVALID_ARG : LBM_OK;
 }
 
-template <int CP16>
+template <int CP16, bool FULL>
 lbm_status conv_tc_launch(const float* x, const TcConv& s, size_t bytes, const float* wt, const float* bias,
                           int relu, float* y, cudaStream_t st)
 {
-    if (cudaFuncSetAttribute(k_conv3d_tc<CP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+    if (cudaFuncSetAttribute(k_conv3d_tc<CP16, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
         cudaSuccess)
         return LBM_ERR_CUDA;
-    const int per_sm = resident_ctas(k_conv3d_tc<CP16>, bytes, s.tcols), sms = sm_count();
+    const int per_sm = resident_ctas(k_conv3d_tc<CP16, FULL>, bytes, s.tcols), sms = sm_count();
     if (per_sm < 1 || sms < 1) return LBM_ERR_CUDA;
     const long long grid = (long long)sms * per_sm;
-    k_conv3d_tc<CP16><<<(unsigned)(grid < s.tiles ? grid : s.tiles), kRows, bytes, st>>>(x, wt, bias, s, relu, y);
+    k_conv3d_tc<CP16, FULL>
+        <<<(unsigned)(grid < s.tiles ? grid : s.tiles), kRows, bytes, st>>>(x, wt, bias, s, relu, y);
     return launched();
 }
 
 lbm_status conv_tc(const float* x, const TcConv& s, size_t bytes, const float* wt, const float* bias, int relu,
                    float* y, cudaStream_t st)
 {
+    const bool full = s.cin == s.cp;
     switch (s.cp / 16) {
-    case 1: return conv_tc_launch<1>(x, s, bytes, wt, bias, relu, y, st);
-    case 2: return conv_tc_launch<2>(x, s, bytes, wt, bias, relu, y, st);
-    case 3: return conv_tc_launch<3>(x, s, bytes, wt, bias, relu, y, st);
-    case 4: return conv_tc_launch<4>(x, s, bytes, wt, bias, relu, y, st);
-    default: return conv_tc_launch<0>(x, s, bytes, wt, bias, relu, y, st);
+    case 1: return full ? conv_tc_launch<1, true>(x, s, bytes, wt, bias, relu, y, st)
+                        : conv_tc_launch<1, false>(x, s, bytes, wt, bias, relu, y, st);
+    case 2: return full ? conv_tc_launch<2, true>(x, s, bytes, wt, bias, relu, y, st)
+                        : conv_tc_launch<2, false>(x, s, bytes, wt, bias, relu, y, st);
+    case 3: return full ? conv_tc_launch<3, true>(x, s, bytes, wt, bias, relu, y, st)
+                        : conv_tc_launch<3, false>(x, s, bytes, wt, bias, relu, y, st);
+    case 4: return full ? conv_tc_launch<4, true>(x, s, bytes, wt, bias, relu, y, st)
+                        : conv_tc_launch<4, false>(x, s, bytes, wt, bias, relu, y, st);
+    default: return conv_tc_launch<0, false>(x, s, bytes, wt, bias, relu, y, st);
     }
 }
 

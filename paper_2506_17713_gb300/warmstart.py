@@ -35,7 +35,7 @@ def flow_case(n):
 
 def sample_solid(n, seed, porosity):
     from synth import grf_porous_medium
-    solid, _ = grf_porous_medium((n, n, n), porosity, 6.0, seed, buffer=0)
+    solid, _ = grf_porous_medium((n, n, n), porosity, 6.0, seed, buffer=0, periodic_x=True)
     return solid
 
 

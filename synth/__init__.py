@@ -164,19 +164,37 @@ def percolating_pores(pore):
     return np.isin(lab, keep), True
 
 
-def grf_porous_medium(shape_xyz, porosity, corr_length, seed, buffer=8, max_seeds=50):
+def periodic_percolating_pores(pore):
+    """Keep only the pore cluster(s) (6-connected) joined to their own periodic image
+    along x, i.e. the clusters that carry flow through a box periodic in x. The box
+    is doubled along x and labelled; a cluster percolates when some voxel and its copy
+    one period further share a label. Returns (pore mask, percolates?)."""
+    n = pore.shape[-1]
+    lab, count = _label_6(np.concatenate([pore, pore], axis=-1))
+    if count == 0:
+        return pore & False, False
+    a, b = lab[..., :n], lab[..., n:]
+    keep = np.unique(a[(a == b) & (a != 0)])
+    if keep.size == 0:
+        return pore & False, False
+    return np.isin(a, keep), True
+
+
+def grf_porous_medium(shape_xyz, porosity, corr_length, seed, buffer=8, max_seeds=50, periodic_x=False):
     """Solid mask (uint8, 1 = solid) of a thresholded Gaussian random field.
 
     The porous block fills x in [buffer, nx - buffer); pores are the lowest
     `porosity` quantile of the field; pores not connected inlet-to-outlet are
-    filled; `buffer` fluid layers sit at both x ends. If a seed does not
-    percolate the next seed (seed + 1, ...) is taken. Returns (solid, seed_used)."""
+    filled; `buffer` fluid layers sit at both x ends. With periodic_x (and no
+    buffer) the pores kept are those joined to their periodic image along x. If a
+    seed does not percolate the next seed (seed + 1, ...) is taken. Returns
+    (solid, seed_used)."""
     nx, ny, nz = shape_xyz
     for s in range(seed, seed + max_seeds):
         g = gaussian_random_field((nx - 2 * buffer, ny, nz), corr_length, s)
         thr = np.quantile(g, porosity)
         pore = g <= thr
-        pore, ok = percolating_pores(pore)
+        pore, ok = periodic_percolating_pores(pore) if periodic_x else percolating_pores(pore)
         if not ok:
             continue
         solid = np.zeros((nz, ny, nx), dtype=np.uint8)
