@@ -483,9 +483,13 @@ def run_warmstart(args):
         t_inf = time.perf_counter() - t0
         sw, tw, kw, _, _, _ = ws.relax(n, solid, pred, rho0=rho_pred)
         rows.append((sp, tp, sw, tw + t_inf, kp, kw))
-        # bounds: start from the converged velocity alone, and from velocity and density
+        # bounds: start from the converged velocity alone, and from velocity and density;
+        # diagnostics: the predicted shape at the true scale, and the prediction without density
+        true_scale = ws.scale_of(u_plain, solid) / ws.scale_of(pred, solid)
         ideal.append((ws.relax(n, solid, u_plain.astype(np.float64))[0],
-                      ws.relax(n, solid, u_plain.astype(np.float64), rho0=rho_plain.astype(np.float64))[0]))
+                      ws.relax(n, solid, u_plain.astype(np.float64), rho0=rho_plain.astype(np.float64))[0],
+                      ws.relax(n, solid, pred * true_scale, rho0=rho_pred)[0],
+                      ws.relax(n, solid, pred)[0]))
         pred_err.append(float(np.linalg.norm(pred - u_plain) / np.linalg.norm(u_plain)))
         scale_err.append(ws.scale_of(pred, solid) / ws.scale_of(u_plain, solid))
     r = np.array(rows)
@@ -509,7 +513,9 @@ def run_warmstart(args):
         "steps_to_steady": {"plain_mean": float(r[:, 0].mean()), "warm_mean": float(r[:, 2].mean()),
                             "ratio": round(float(r[:, 0].sum() / r[:, 2].sum()), 3),
                             "from_converged_velocity_mean": float(np.mean([i[0] for i in ideal])),
-                            "from_converged_velocity_and_density_mean": float(np.mean([i[1] for i in ideal]))},
+                            "from_converged_velocity_and_density_mean": float(np.mean([i[1] for i in ideal])),
+                            "predicted_shape_and_density_at_true_scale_mean": float(np.mean([i[2] for i in ideal])),
+                            "predicted_velocity_without_density_mean": float(np.mean([i[3] for i in ideal]))},
         "prediction_rel_l2_error_mean": round(float(np.mean(pred_err)), 4),
         "predicted_over_true_scale": [round(float(v), 3) for v in scale_err],
         "scale_fit": [round(float(c), 4) for c in coef],

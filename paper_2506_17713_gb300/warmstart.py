@@ -4,10 +4,10 @@ learned initial fields in Section 1 but defines no network).
 Workload: single-phase flow through periodic porous samples (thresholded Gaussian
 random fields) under a body force, the permeability estimate of Section 3.4. A 3-D
 U-Net maps the fluid indicator of a sample to its steady velocity field, scaled as
-nu u / a (a "local permeability", independent of the force). A steady-state run
-then starts from rho = 1 and the predicted velocity instead of from rest, and
-relaxes to the same residual (||u^n - u^{n-100}||_2 / ||u^n||_2 <= 1e-6); the plain
-run from rest is the fallback and the judge of the prediction.
+nu u / a (a "local permeability", independent of the force), and its density
+deviation. A steady-state run then starts from the predicted density and velocity
+instead of from rest, and relaxes to the same residual (||u^n - u^{n-100}||_2 / ||u^n||_2 <= 1e-6); the plain
+run from rest is the fallback and the arbiter of the prediction.
 
 Every operation of the network runs in the project's CUDA kernels (nn.py /
 include/lbm_nn.h); torch only provides device memory.
