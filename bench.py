@@ -610,6 +610,17 @@ def run_ours(args):
                "steps": args.e2e_steps,
                "note": "init_fields from pinned host + steps + macroscopic to pinned host + diagnostics"}
 
+    # --- ceiling of the collide pass's access pattern: free streaming with the same gather,
+    # launch shape and population traffic, no arithmetic and no psi (replaces the state)
+    pattern = None
+    if not fused and args.probe_steps > 0:
+        t_str = lat.stream_probe(args.probe_steps) / args.probe_steps / 1e3
+        sbytes = abytes["collide"] - K * (8 if case.get("real") == "f64" else 4)   # without the psi read
+        ach_str = sbytes * units / t_str / 1e9
+        pattern = {"kernel": "k_stream", "bytes_per_lu": sbytes, "ms_per_launch": round(t_str * 1e3, 4),
+                   "achieved": round(ach_str, 1), "frac_of_peak": round(ach_str / peak, 4),
+                   "collide_frac_of_pattern": round(ach_col / ach_str, 4)}
+
     if rank != 0:
         barrier(world, dev)
         return
@@ -653,7 +664,8 @@ def run_ours(args):
                                         "bytes_per_lu": abytes["density"],
                                         "ms_per_launch": round(t_den * 1e3, 4)},
                      "step": {"bytes_per_lu": abytes["step"], "achieved": round(step_gbs, 1),
-                              "frac": round(step_gbs / peak, 4)}},
+                              "frac": round(step_gbs / peak, 4)},
+                     "access_pattern_ceiling": pattern},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -680,6 +692,8 @@ def main():
     ap.add_argument("--n", type=int, default=256, help="cube edge (256 = the benchmark workload; "
                     "smaller edges are for profiling captures)")
     ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--probe-steps", type=int, default=50,
+                    help="launches of the free-streaming probe of the collide access pattern (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="CPU time of the oracle sample behind cpu_baseline")
     ap.add_argument("--ref-steps", type=int, default=3)

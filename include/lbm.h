@@ -208,6 +208,16 @@ lbm_status lbm_sync(lbm_ctx* ctx);
  * slot holds the single-pass kernel. */
 lbm_status lbm_profile_step(lbm_ctx* ctx, int nsteps, double* ms, long long* launches);
 
+/* Bandwidth probe of the collide pass's access pattern: nsteps launches of a kernel that
+ * gathers the post-stream populations of every fluid node exactly as the collide pass
+ * does (pull streaming, bounce-back, the same launch shape) and stores them unchanged in
+ * the other buffer -- free streaming, no collision, force or psi. *ms receives the summed
+ * device time (milliseconds, CUDA events on the context stream, synchronised after each
+ * launch). The populations end streamed nsteps times: this replaces the state of the
+ * lattice, so it is for benchmarks on a context that is not needed afterwards. No
+ * counterpart in the paper. */
+lbm_status lbm_stream_probe(lbm_ctx* ctx, int nsteps, double* ms);
+
 /* Number of kernels this context has launched since creation. */
 long long lbm_kernel_launches(const lbm_ctx* ctx);
 

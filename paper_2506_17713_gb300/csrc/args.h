@@ -86,7 +86,8 @@ enum : int {
     OP_GET_POPS = 5,     // gather post-stream populations into an array
     OP_MACRO = 6,        // rho, u = (j + F/2) / rho into arrays
     OP_DIAG = 7,         // mass / momentum / residual partial sums (deterministic)
-    OP_FUSED = 8         // single-pass step (periodic, no solids, D3Q19)
+    OP_FUSED = 8,        // single-pass step (periodic, no solids, D3Q19)
+    OP_STREAM = 9        // free streaming only: gathered populations stored unchanged (bandwidth probe)
 };
 
 template <typename T>

@@ -1246,6 +1246,28 @@ __global__ void __launch_bounds__(256, K == 1 ? 4 : 2) k_collide(const KArgs<T> 
     if (fluid_node<GEOM>(a, nd)) collide_node<L, T, S, K, COLL, GEOM>(a, nd);
 }
 
+// Free streaming without collision, forcing or psi: the post-stream populations of
+// every fluid node, gathered as the collide pass gathers them, are stored unchanged
+// in the destination buffer. Same launch shape and population traffic as the collide
+// pass (Q reads and Q writes per component and node) without its arithmetic and its
+// psi stencil, so the bandwidth it reaches is the ceiling of that access pattern.
+template <class L, typename T, typename S, int K, bool GEOM>
+__global__ void __launch_bounds__(256, K == 1 ? 4 : 2) k_stream(const KArgs<T> a)
+{
+    Node nd;
+    if (!fluid_node<GEOM>(a, nd)) return;
+    const Params<T>& P = a.p;
+    const long long N = P.N;
+    T f[K][L::Q];
+    gather_all<L, T, S, K, GEOM>(a.f_src, P, a.solid, a.fidx, nd, geo3<GEOM>(P, nd.x, nd.y, nd.z), f);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        S* dst = static_cast<S*>(a.f_dst) + (long long)k * L::Q * N + (a.fidx ? nd.slot : nd.n);
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) store_pop<L, T, S>(dst, (long long)i * N, i, f[k][i], P.rho_ref[k]);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Single-pass step for periodic lattices without solids (D3Q19)
 // ---------------------------------------------------------------------------
@@ -1684,6 +1706,7 @@ cudaError_t run_k(int op, const KArgs<T>& a)
         if (a.n_bsolid > 0) k_virtual<L, T, K><<<(a.n_bsolid + 255) / 256, 256, 0, a.stream>>>(a);
         break;
     case OP_COLLIDE: k_collide<L, T, S, K, COLL, GEOM><<<gz, bz, 0, a.stream>>>(a); break;
+    case OP_STREAM: k_stream<L, T, S, K, GEOM><<<gz, bz, 0, a.stream>>>(a); break;
     case OP_FUSED:
         if constexpr (L::D == 3 && !GEOM) {
             constexpr int TX = 32, TY = 8;

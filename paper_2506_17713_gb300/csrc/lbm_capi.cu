@@ -899,9 +899,42 @@ lbm_status profile_t(lbm_ctx* c, int nsteps, double* ms, long long* nl, const Pa
     }
     return check_status_word(c);
 }
+template <typename T>
+lbm_status stream_probe_t(lbm_ctx* c, int nsteps, double* ms, const Params<T>& P)
+{
+    cudaEvent_t ev[2];
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return fail_cuda(c, cudaErrorUnknown);
+    double acc = 0.0;
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < nsteps && e == cudaSuccess; ++s) {
+        KArgs<T> a = base_args<T>(c, P);
+        e = cudaEventRecord(ev[0], c->stream);
+        if (e == cudaSuccess) e = dispatch<T>(c, OP_STREAM, a);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        if (e != cudaSuccess) break;
+        c->cur ^= 1;
+        float t = 0.0f;
+        e = cudaEventElapsedTime(&t, ev[0], ev[1]);
+        acc += t;
+    }
+    for (auto& x : ev) cudaEventDestroy(x);
+    if (e != cudaSuccess) return fail_cuda(c, e);
+    if (ms) *ms = acc;
+    return LBM_OK;
+}
 }  // namespace
 
 extern "C" {
+
+lbm_status lbm_stream_probe(lbm_ctx* c, int nsteps, double* ms)
+{
+    if (!c || nsteps < 0) return LBM_ERR_INVALID_ARG;
+    if (c->sticky != LBM_OK) return c->sticky;
+    if (!ready(c)) return LBM_ERR_STATE;
+    return c->elt == 8 ? stream_probe_t<double>(c, nsteps, ms, c->pd) : stream_probe_t<float>(c, nsteps, ms, c->pf);
+}
 
 lbm_status lbm_profile_step(lbm_ctx* c, int nsteps, double* ms, long long* launches)
 {

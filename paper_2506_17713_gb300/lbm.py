@@ -29,7 +29,7 @@ LBM_HOST, LBM_DEVICE = 0, 1
 EXPORTS = ["lbm_workspace_size", "lbm_create", "lbm_set_geometry", "lbm_init_fields", "lbm_step",
            "lbm_macroscopic", "lbm_diagnostics", "lbm_get_populations", "lbm_set_populations",
            "lbm_velocity_set", "lbm_sync", "lbm_kernel_launches", "lbm_temperature", "lbm_destroy",
-           "lbm_status_str", "lbm_profile_step", "lbm_mass_noalloc", "lbm_batch_workspace_size",
+           "lbm_status_str", "lbm_profile_step", "lbm_stream_probe", "lbm_mass_noalloc", "lbm_batch_workspace_size",
            "lbm_batch_create", "lbm_batch_autotune", "lbm_batch_step", "lbm_batch_launches",
            "lbm_batch_destroy"]
 
@@ -87,6 +87,7 @@ def library():
     L.lbm_kernel_launches.restype = C.c_longlong
     L.lbm_temperature.argtypes = [vp, C.c_int, dp]
     L.lbm_profile_step.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_longlong)]
+    L.lbm_stream_probe.argtypes = [vp, C.c_int, dp]
     L.lbm_mass_noalloc.argtypes = [pp, vp, dp, vp]
     L.lbm_batch_workspace_size.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(sz)]
     L.lbm_batch_create.argtypes = [C.POINTER(vp), C.c_int, vp, sz, vp, C.POINTER(vp)]
@@ -188,6 +189,13 @@ def lbm_temperature(ctx, comp):
     T = C.c_double(0.0)
     _check(library().lbm_temperature(ctx, comp, C.byref(T)), "lbm_temperature")
     return T.value
+
+
+def lbm_stream_probe(ctx, nsteps):
+    """summed milliseconds of nsteps free-streaming launches (replaces the lattice state)"""
+    ms = C.c_double(0.0)
+    _check(library().lbm_stream_probe(ctx, int(nsteps), C.byref(ms)), "lbm_stream_probe")
+    return ms.value
 
 
 def lbm_profile_step(ctx, nsteps):
@@ -387,6 +395,9 @@ class Lattice:
 
     def profile_step(self, n):
         return lbm_profile_step(self.ctx, n)
+
+    def stream_probe(self, n):
+        return lbm_stream_probe(self.ctx, n)
 
     def temperature(self, comp=0):
         return lbm_temperature(self.ctx, comp)
