@@ -29,6 +29,7 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     "pr256": "D3Q19 Shan-Chen PR T=0.6Tc MRT 256^3 FP32, 8 droplets (seed 1234)",
     "exp256": "D3Q19 Shan-Chen psi=exp(-1/rho) BGK 256^3 FP32, droplet R=30",
+    "cs128": "D2Q9 Shan-Chen CS T=0.7Tc BGK 128^2 FP64, droplet R=25 (the small parity case; L2-resident)",
     "porous400": "D3Q19 two-component Shan-Chen 400^3 FP32, GRF porous medium (porosity 0.15, "
                  "corr. length 6, seed 7), wetting, constant-density x faces",
     "warmstart": "learned warm start of single-phase steady-state runs: D3Q19 BGK, periodic GRF porous "
@@ -64,6 +65,8 @@ def make_case(name, n=256):
                                               width=max(2.0, cases.PR06_WIDTH * f))
     elif name == "exp256":
         case, init = cases.droplet_3d_exp(n=n, radius=30.0 * n / 256)
+    elif name == "cs128":
+        case, init = cases.droplet_2d_cs(n=128 if n == 256 else n)
     elif name == "batch64":   # the oracle-timed stand-in: the first sample of the batch
         case, init = cases.sphere_pack_batch(count=1)[0]
     elif name == "porous400":
@@ -72,6 +75,22 @@ def make_case(name, n=256):
     else:
         raise SystemExit("unknown workload " + name)
     return case, init
+
+
+def macroscopic_layout(case):
+    """(element type name, velocity rows) of what lbm_macroscopic writes: the compute
+    type (double for FP64 lattices, float otherwise) and D velocity components"""
+    return ("float64" if case.get("real") == "f64" else "float32"), (3 if case["lattice"] == "D3Q19" else 2)
+
+
+def l2_note(case, K, N):
+    Q = 19 if case["lattice"] == "D3Q19" else 9
+    ep = {"f16s": 2, "bf16s": 2, "f64": 8}.get(case.get("real", "f32"), 4)
+    gb = K * Q * N * ep / 1e9
+    if 2 * gb > 0.129:
+        return "inputs larger than L2 (two %.2f GB population buffers)" % gb
+    return ("inputs L2-resident (two %.1f MB population buffers): a launch- and latency-bound case, "
+            "not an HBM measurement" % (gb * 1e3))
 
 
 def algorithmic_bytes(case, fused=False, fluid_list=False):
@@ -267,7 +286,7 @@ def run_reference(args):
     nx, ny, nz = case["shape"]
     sample = "%d oracle steps on the full %dx%dx%d lattice (FP64, OpenMP)" % (steps, nx, ny, nz)
     line = {
-        "impl": "reference", "metric": "D3Q19 Shan-Chen MLUPS", "value": round(mlups, 3),
+        "impl": "reference", "metric": "%s Shan-Chen MLUPS" % case["lattice"], "value": round(mlups, 3),
         "unit": "MLUPS", "n_gpus": args.gpus, "steps": steps, "warmup": 1,
         "ms_per_step": round(1e3 * dt / steps, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -593,8 +612,10 @@ def run_ours(args):
     e2e = None
     if args.e2e_steps > 0:
         rho_h = [torch.from_numpy(np.ascontiguousarray(r, dtype=np.float64)).pin_memory() for r in init["rho"]]
-        out_rho = torch.empty((nz, ny, nx), dtype=torch.float32).pin_memory()
-        out_u = torch.empty((3, nz, ny, nx), dtype=torch.float32).pin_memory()
+        out_t, dims = macroscopic_layout(case)
+        out_t = getattr(torch, out_t)
+        out_rho = torch.empty((nz, ny, nx), dtype=out_t).pin_memory()
+        out_u = torch.empty((dims, nz, ny, nx), dtype=out_t).pin_memory()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k, r in enumerate(rho_h):
@@ -606,7 +627,8 @@ def run_ours(args):
         te_max = reduce_max(te, world, dev)
         e2e = {"value": round(aggregate(K * N * args.e2e_steps, te_max, world) / 1e6, 1), "unit": "MLUPS",
                "h2d_bytes_per_step": int(sum(r.numel() for r in rho_h) * 8 // args.e2e_steps),
-               "d2h_bytes_per_step": int((out_rho.numel() + out_u.numel()) * 4 // args.e2e_steps + 48 * K),
+               "d2h_bytes_per_step": int((out_rho.numel() + out_u.numel()) * out_rho.element_size()
+                                         // args.e2e_steps + 48 * K),
                "steps": args.e2e_steps,
                "note": "init_fields from pinned host + steps + macroscopic to pinned host + diagnostics"}
 
@@ -639,7 +661,7 @@ def run_ours(args):
                "sample": "%d FP64 oracle steps on %s (%.1f s, after one untimed step)" % (csteps, what, cpu_dt)}
 
     line = {
-        "metric": "D3Q19 Shan-Chen MLUPS", "value": round(mlups, 1), "unit": "MLUPS",
+        "metric": "%s Shan-Chen MLUPS" % case["lattice"], "value": round(mlups, 1), "unit": "MLUPS",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * secs_max / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if case.get("real") == "f64" else "f32",
@@ -652,8 +674,7 @@ def run_ours(args):
                    "fluid_nodes": n_fluid, "mflups": round(mlups * n_fluid / N, 1),
                    "storage": STORAGE[case.get("real", "f32")] + (
                        " (rho_ref %.6g)" % case["rho_ref"][0] if "rho_ref" in case else ""),
-                   "l2": "inputs larger than L2 (two %.2f GB population buffers)" % (
-                       K * 19 * N * (2 if case.get("real") in ("f16s", "bf16s") else 4) / 1e9)},
+                   "l2": l2_note(case, K, N)},
         "roofline": {"bound": "hbm", "kernel": "k_fused" if fused else "k_collide", "achieved": round(ach_col, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(ach_col / peak, 4),
                      "peak_kind": peak_kind,

@@ -79,3 +79,13 @@ def test_committed_traffic_is_gated_by_kernel_source_hash(monkeypatch):
     assert bench.committed_traffic("k_collide", "pr256", 128) is None      # no summary for that size
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 64)
     assert bench.committed_traffic("k_collide", "pr256", 256) is None      # kernels changed since the capture
+
+
+def test_macroscopic_output_layout_follows_the_lattice():
+    # lbm_macroscopic writes doubles for FP64 lattices and D velocity rows: the end-to-end
+    # host buffers of the benchmark must match, or the copy overruns them
+    import bench
+    assert bench.macroscopic_layout(bench.make_case("cs128")[0]) == ("float64", 2)
+    assert bench.macroscopic_layout(bench.make_case("pr256", 32)[0]) == ("float32", 3)
+    c = dict(bench.make_case("pr256", 32)[0], real="f16s")
+    assert bench.macroscopic_layout(c) == ("float32", 3)
