@@ -36,6 +36,9 @@ WORKLOADS = {
                  "samples (porosity U[0.1,0.35], corr. length 6), body force; 3-D U-Net trained on LBM steady states",
     "conv3d": "one periodic 3x3x3 convolution layer of the warm-start U-Net (FP32 activations): forward, "
               "adjoint and weight gradient, BF16 tensor cores vs FP32 CUDA cores",
+    "warmstart_errors": "which errors of a warm start cost relaxation steps: the warm-start samples started from "
+                        "their converged field with a scaled magnitude, white or smooth velocity noise, or density "
+                        "noise",
     "batch64": "64 D3Q19 sphere-pack drainage samples, box edges U[64,192] (seed 2024), overlapping spheres "
                "r U[8,12] to porosity 0.38, PR T=0.8Tc MRT FP32, wetting solids, per-sample inlet pressure step",
 }
@@ -461,6 +464,65 @@ def run_conv3d(args):
         "gpu_launches": launches, "clocks": clk}))
 
 
+def _smooth_in_fluid(u, solid, it):
+    """`it` Jacobi sweeps of the 7-point mean over fluid nodes (solids stay 0)"""
+    fl = (solid == 0).astype(np.float64)
+    v = u * fl
+    for _ in range(it):
+        acc, cnt = v.copy(), fl.copy()
+        for ax in (-1, -2, -3):
+            for sh in (1, -1):
+                acc += np.roll(v, sh, axis=ax)
+                cnt += np.roll(fl, sh, axis=ax)
+        v = np.where(fl > 0, acc / np.maximum(cnt, 1), 0.0)
+    return v
+
+
+def run_warmstart_errors(args):
+    """Steps to the residual criterion from perturbed converged fields of the warm-start
+    samples (the first --ws-test held-out seeds, capped at 4): what kind of error in a
+    predicted start the relaxation pays for."""
+    import torch
+    from paper_2506_17713_gb300 import warmstart as ws
+    from synth import uniform
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    n, ntrain = args.ws_n, args.ws_train
+    phis = [0.10 + 0.25 * float(v) for v in uniform(4242, ntrain + args.ws_test)]
+    rng = np.random.default_rng(0)
+    rows = []
+    for j in range(min(4, args.ws_test)):
+        solid = ws.sample_solid(n, 5000 + j, phis[ntrain + j])
+        fl = solid == 0
+        sp, _, _, _, up, rp = ws.relax(n, solid, None)
+        up, rp = up.astype(np.float64), rp.astype(np.float64)
+        U = np.abs(up[0][fl]).mean()
+        r = {"porosity": round(phis[ntrain + j], 4), "rest": sp}
+        r["exact_velocity"] = ws.relax(n, solid, up)[0]
+        r["exact_velocity_and_density"] = ws.relax(n, solid, up, rho0=rp)[0]
+        r["0.7x_velocity_exact_density"] = ws.relax(n, solid, 0.7 * up, rho0=rp)[0]
+        r["1.5x_velocity_exact_density"] = ws.relax(n, solid, 1.5 * up, rho0=rp)[0]
+        white = rng.standard_normal(up.shape) * 0.3 * U * fl
+        r["velocity_plus_30pct_white_noise_exact_density"] = ws.relax(n, solid, up + white, rho0=rp)[0]
+        sm = _smooth_in_fluid(rng.standard_normal(up.shape) * fl, solid, 6)
+        sm *= 0.3 * U / max(np.abs(sm[0][fl]).mean(), 1e-30)
+        r["velocity_plus_30pct_smooth_noise_exact_density"] = ws.relax(n, solid, up + sm, rho0=rp)[0]
+        dn = 0.01 * (rp - 1.0).std() * rng.standard_normal(rp.shape)
+        r["exact_velocity_density_plus_1pct_noise"] = ws.relax(n, solid, up, rho0=rp + dn)[0]
+        rows.append(r)
+    if rank != 0:
+        return
+    keys = [k for k in rows[0] if k != "porosity"]
+    print(json.dumps({
+        "metric": "steps to residual <= 1e-6 by start (mean over samples)", "value": float(np.mean([r["rest"] for r in rows])),
+        "unit": "steps", "n_gpus": world, "steps": int(sum(sum(r[k] for k in keys) for r in rows)), "warmup": 0,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS["warmstart_errors"], "edge": n, "samples": len(rows),
+                   "noise": "relative to the mean |u_x| over the fluid; density noise relative to the std of rho - 1"},
+        "mean_steps": {k: float(np.mean([r[k] for r in rows])) for k in keys},
+        "per_sample": rows, "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None}), flush=True)
+
+
 def run_warmstart(args):
     """Time to steady state (residual <= 1e-6) of held-out samples, from the network's
     prediction vs from rest; the network is trained in the same run on steady states
@@ -744,6 +806,8 @@ def main():
         run_batch(args)
     elif args.workload == "warmstart":
         run_warmstart(args)
+    elif args.workload == "warmstart_errors":
+        run_warmstart_errors(args)
     elif args.workload == "conv3d":
         run_conv3d(args)
     else:
