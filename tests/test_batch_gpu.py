@@ -164,3 +164,23 @@ def test_incompatible_or_repeated_lattices_are_rejected():
     with pytest.raises(LbmError) as ei:
         Batch([a, a])
     assert ei.value.status == 1
+
+
+def test_full_size_batch_matches_single_lattices_bitwise():
+    # the 64-sample benchmark batch (edges U[64, 192]) in its benchmark launch
+    # configuration (autotuned, graph replays); the smallest and the largest sample
+    # are stepped on their own as well and must end bit for bit equal
+    from paper_2506_17713_gb300 import Batch
+    samples = cases.sphere_pack_batch(count=64)
+    lats = [_lattice(c, i) for c, i in samples]
+    sizes = [l.N for l in lats]
+    pick = [int(np.argmin(sizes)), int(np.argmax(sizes))]
+    refs = [_lattice(*samples[j]) for j in pick]
+    batch = Batch(lats)
+    batch.autotune()
+    batch.step(4)
+    for r in refs:
+        r.step(4)
+    _same([lats[j] for j in pick], refs)
+    m, _ = lats[pick[1]].diagnostics()
+    assert np.isfinite(m).all()
