@@ -1665,7 +1665,7 @@ __device__ __forceinline__ bool node_of_unit(const KArgs<T>& a, long long t, Nod
 }
 
 template <class L, typename T, typename S, int K, int COLL, bool GEOM, int BOP>
-__global__ void __launch_bounds__(256, BOP == BOP_COLLIDE ? (K == 1 ? 4 : 2) : (K == 1 ? 0 : 5))
+__global__ void __launch_bounds__(256, BOP == BOP_COLLIDE ? (K == 1 ? 4 : 2) : (K == 1 ? 0 : 4))
 kb_pass(const BatchItem<T>* __restrict__ items, int n_items, long long nvb, int parity)
 {
     __shared__ __align__(16) unsigned char sbuf[sizeof(KArgs<T>)];
