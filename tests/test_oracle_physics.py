@@ -1,6 +1,7 @@
 """Physics pins of the FP64 oracle: closed forms the whole time step must reproduce.
 
 Poiseuille flow (exact for BGK halfway bounce-back at tau = 1/2 + sqrt(3/16)),
+cocurrent two-layer channel flow against its layered Stokes solution (Section 3.4.2),
 flat-interface coexistence against the Maxwell construction (Section 3.1),
 Laplace's law (Section 3.2), neutral wetting (phi = 1, drho = 0 gives 90
 degrees, Section 3.3.2) and the monotone effect of phi / drho (Section 2.4).
@@ -138,3 +139,65 @@ def test_wetting_parameters_move_contact_angle():
     hydrophobic = _sessile(1.0, 0.04, steps=4000)
     assert hydrophilic < neutral - 10
     assert hydrophobic > neutral + 10
+
+
+def test_cocurrent_two_layer_channel_against_closed_form():
+    # Section 3.4.2, relative permeabilities of cocurrent flow in a channel: a
+    # non-wetting core |y| < b between wetting films b < |y| < H, driven by the same
+    # acceleration a, walls half a link outside the end nodes. Steady Stokes flow in
+    # each layer with continuous velocity and shear stress at |y| = b:
+    #   core  u = u_film(b) + G_nw (b^2 - y^2) / (2 mu_nw)
+    #   film  u = G_w (H^2 - y^2) / (2 mu_w) - c (H - |y|),  c = (G_w - G_nw) b / mu_w,
+    # with G = a (rho_1 + rho_2) and mu = sum_k rho_k nu_k (common-velocity mixture) of
+    # each layer's bulk; b is where the two densities cross. For G_w = G_nw the layer
+    # fluxes give K_rw = S_w^2 (3 - S_w) / 2 and K_rnw = (1 - S_w)[3M/2 + (1 - S_w)^2 (1 - 3M/2)],
+    # M = mu_nw / mu_w, S_w = 1 - b / H (checked here on the closed form itself).
+    H2, a, g12 = 80, 1e-6, 0.4
+    tau_w, tau_nw = 0.5 + np.sqrt(3.0 / 16.0), 0.7        # exact halfway wall for the film
+    case = cases.base_case("D2Q9", (4, H2, 1), ncomp=2, psi=["rho", "rho"], velocity="common",
+                           g=[[0.0, g12], [g12, 0.0]], tau=[tau_w, tau_nw], accel=[[a, 0, 0], [a, 0, 0]],
+                           bc=["periodic", "periodic", "wall", "wall", "periodic", "periodic"])
+    s = oracle.OracleSim(case)
+    y = np.arange(H2) + 0.5 - H2 / 2
+    core = 0.5 * (1 - np.tanh(2 * (np.abs(y) - 20.0) / 5.0))
+    ones = np.ones((1, H2, 4))
+    s.init_fields(0, (0.05 + 0.95 * (1 - core))[None, :, None] * ones)
+    s.init_fields(1, (0.05 + 0.95 * core)[None, :, None] * ones)
+    s.step(140000)
+    u_prev = s.macroscopic(-1)[1][0][0, :, 0].copy()
+    s.step(10000)
+    u = s.macroscopic(-1)[1][0][0, :, 0]
+    assert np.abs(u - u_prev).max() < 1e-7 * u.max()                     # steady
+    r_w, r_nw = s.macroscopic(0)[0][0, :, 0], s.macroscopic(1)[0][0, :, 0]
+    assert min(r_w.min(), r_nw.min()) > 0.0
+    up = np.arange(H2 // 2, H2)
+    d = (r_nw - r_w)[up]
+    i = int(np.argmax(d < 0))
+    b = y[up][i - 1] + d[i - 1] / (d[i - 1] - d[i])
+    H = H2 / 2
+    nu_w, nu_nw = (tau_w - 0.5) / 3.0, (tau_nw - 0.5) / 3.0
+    jw, jn = 2, H2 // 2                                                    # bulk film / core nodes
+    G_w, G_nw = a * (r_w[jw] + r_nw[jw]), a * (r_w[jn] + r_nw[jn])
+    mu_w, mu_nw = r_w[jw] * nu_w + r_nw[jw] * nu_nw, r_w[jn] * nu_w + r_nw[jn] * nu_nw
+    c = (G_w - G_nw) * b / mu_w
+    ay = np.abs(y)
+    u_film = G_w * (H ** 2 - ay ** 2) / (2 * mu_w) - c * (H - ay)
+    u_b = G_w * (H ** 2 - b ** 2) / (2 * mu_w) - c * (H - b)
+    u_ref = np.where(ay <= b, u_b + G_nw * (b ** 2 - ay ** 2) / (2 * mu_nw), u_film)
+    film, coremask = ay > b, ay <= b
+    assert 0.3 < mu_nw / mu_w < 0.6 and 15 < b < 25
+    assert np.abs(u - u_ref).max() < 0.03 * u_ref.max()
+    assert abs(u[film].sum() / u_ref[film].sum() - 1) < 0.02
+    assert abs(u[coremask].sum() / u_ref[coremask].sum() - 1) < 0.02
+    # the closed form with equal layer forces reproduces the relative permeabilities
+    Sw, M = 1 - b / H, mu_nw / mu_w
+    G = 0.5 * (G_w + G_nw)
+    yy = np.linspace(0.0, H, 200001)
+    uu = np.where(yy <= b, G * (H ** 2 - b ** 2) / (2 * mu_w) + G * (b ** 2 - yy ** 2) / (2 * mu_nw),
+                  G * (H ** 2 - yy ** 2) / (2 * mu_w))
+    q0 = 2 * H ** 3 / 3 * G
+    trap = getattr(np, "trapezoid", None) or np.trapz
+    qw = 2 * trap(np.where(yy > b, uu, 0.0), yy)
+    qn = 2 * trap(np.where(yy <= b, uu, 0.0), yy)
+    assert abs(qw / (q0 / mu_w) - 0.5 * Sw ** 2 * (3 - Sw)) < 1e-6
+    assert abs(qn / (q0 / mu_nw) - (1 - Sw) * (1.5 * M + (1 - Sw) ** 2 * (1 - 1.5 * M))) < 1e-6
