@@ -266,7 +266,7 @@ def oracle_sample(case, init, steps=None, seconds=None):
         t0 = time.perf_counter()
         s.step(1)
         dt = time.perf_counter() - t0
-        steps = int(min(1000, max(1, round(seconds / max(dt, 1e-6)))))
+        steps = int(min(200000, max(1, round(seconds / max(dt, 1e-6)))))
         steps_left = steps - 1
     else:
         steps_left = steps
