@@ -504,6 +504,9 @@ def run_warmstart_errors(args):
         r["1.5x_velocity_exact_density"] = ws.relax(n, solid, 1.5 * up, rho0=rp)[0]
         white = rng.standard_normal(up.shape) * 0.3 * U * fl
         r["velocity_plus_30pct_white_noise_exact_density"] = ws.relax(n, solid, up + white, rho0=rp)[0]
+        r["velocity_plus_10pct_white_noise_exact_density"] = ws.relax(n, solid, up + white / 3, rho0=rp)[0]
+        r["velocity_plus_3pct_white_noise_exact_density"] = ws.relax(n, solid, up + white / 10, rho0=rp)[0]
+        r["velocity_plus_10pct_white_noise_density_1"] = ws.relax(n, solid, up + white / 3)[0]
         sm = _smooth_in_fluid(rng.standard_normal(up.shape) * fl, solid, 6)
         sm *= 0.3 * U / max(np.abs(sm[0][fl]).mean(), 1e-30)
         r["velocity_plus_30pct_smooth_noise_exact_density"] = ws.relax(n, solid, up + sm, rho0=rp)[0]
