@@ -67,6 +67,16 @@ enum { LBM_EOS_CS = 0, LBM_EOS_PR = 1, LBM_EOS_VDW = 2, LBM_EOS_RK = 3, LBM_EOS_
  * (x faces only) */
 enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL = 1, LBM_BC_PRESSURE = 2 };
 enum { LBM_HOST = 0, LBM_DEVICE = 1 };
+/* forcing of the collision: the Exact Difference Method of Eq. edm (default), or the
+ * moment-space forcing F_m that Eq. mrt_surface (Section 2.3) places inside M^-1[...] next
+ * to the relaxation -- the scheme of Li et al. (2013) for the surface-tension adjustment,
+ * i.e. the forcing of Guo et al. (2002) in moment space: equilibrium at the physical
+ * velocity v = u + F/(2 rho), source (I - S/2) M S_i with
+ * S_i = w_i [(e_i - v)/c_s^2 + (e_i.v) e_i/c_s^4].F. It equals the EDM update minus S
+ * applied to the moments of rho du du / 4 (du = F/rho), so it lacks EDM's F F / rho stress,
+ * and with it the surface tension scales with 1 - kappa as Section 2.3 states. D2Q9 only
+ * (LBM_ERR_INVALID_ARG for D3Q19), BGK or MRT. */
+enum { LBM_FORCING_EDM = 0, LBM_FORCING_MOMENT = 1 };
 /* kernel schedule of a step. AUTO and TWO_PASS: a density pass (psi to HBM) and a collide
  * pass, back to back. SLAB_OVERLAP (D3Q19 lattices of 64 or more planes without solids,
  * else TWO_PASS): the same two passes over z slabs of about 32 planes, overlapped on two
@@ -138,6 +148,7 @@ typedef struct lbm_params {
                                             + A/2 sum_i G_i (psi(x+e_i)^2-psi^2) e_i e_i].
                           0 = off. Nonzero only with D2Q9 and MRT (the paper gives no D3Q19
                           form): LBM_ERR_INVALID_ARG otherwise. */
+    int forcing;       /* LBM_FORCING_EDM (0) | LBM_FORCING_MOMENT (D2Q9) */
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -271,10 +282,11 @@ void lbm_batch_destroy(lbm_batch* b);
 
 /*
  * Mass without allocation. The paper has no counterpart: this is a service for callers
- * that cannot allocate device memory at all -- code running while a CUDA graph is being
- * captured, processes where a framework owns every allocation, or callers whose memory
- * is used up by the lattice itself. It returns the same sums as the mass part of
- * lbm_diagnostics, from populations the caller already holds.
+ * that cannot allocate device memory at all -- processes where a framework owns every
+ * allocation, or callers whose memory is used up by the lattice itself. It returns the
+ * same sums as the mass part of lbm_diagnostics, from populations the caller already
+ * holds. It copies its totals to host memory and synchronises the stream, so it cannot
+ * be called on a stream that is being captured into a CUDA graph (the capture would fail).
  *
  *   p     lattice parameters; lattice, nx, ny, nz, ncomp and real are used.
  *   d_f   device pointer, post-stream populations [ncomp][Q][N] of the real type of p,
@@ -289,10 +301,11 @@ void lbm_batch_destroy(lbm_batch* b);
  * library until the process exits; it holds the partial sums of at most
  * LBM_NOALLOC_MAX_NODES nodes (256^3), and larger lattices are rejected with
  * LBM_ERR_INVALID_ARG before any device work. The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current, so make that
- * first call before any stream capture. Every call shares the array and leaves its last
- * contents there; each call overwrites all it reads. Calls that overlap on the GPU
- * (different streams, or different host threads) race on the array.
+ * array's device address (cudaGetSymbolAddress) with that device current and caches it
+ * for later calls (the cache is safe to fill from several host threads). Every call
+ * shares the array and leaves its last contents there; each call overwrites all it
+ * reads. Calls that overlap on the GPU (different streams, or different host threads)
+ * race on the array.
  */
 #define LBM_NOALLOC_MAX_NODES (256 * 256 * 256)
 lbm_status lbm_mass_noalloc(const lbm_params* p, const void* d_f, double* mass, void* stream);

@@ -96,6 +96,15 @@ lbm_status lbm_nn_conv3d_tc_grad_weight(const float* x, int cin, const float* gy
  * Synchronises the device. */
 lbm_status lbm_nn_tc_error(int* flag);
 
+/* Check of the failure detection above (no counterpart in the paper): one GPU thread waits,
+ * with the same bounded wait the tensor-core kernels use, on an mbarrier that nothing
+ * arrives on, and gives up after limit_cycles SM clock cycles (1 .. 4e9; ~2e6 is about a
+ * millisecond at 2 GHz). *completed receives 1 if the wait ended normally (it cannot
+ * here), 0 if it gave up; a wait that gives up also sets the flag that lbm_nn_tc_error
+ * reads. No tensor memory is allocated and no MMA is in flight. Synchronises the stream;
+ * LBM_ERR_INVALID_ARG for a NULL result or a limit out of range. */
+lbm_status lbm_nn_wait_selftest(long long limit_cycles, int* completed, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

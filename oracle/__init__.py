@@ -37,6 +37,7 @@ class OrcParams(C.Structure):
         ("accel", (C.c_double * 3) * 2),
         ("face_bc", C.c_int * 6), ("face_rho", (C.c_double * 2) * 6),
         ("kappa", C.c_double * 2),
+        ("forcing", C.c_int),
     ]
 
 
@@ -150,6 +151,7 @@ def params_from_case(case):
     for f in range(6):
         for k in range(2):
             p.face_rho[f][k] = br[f, k]
+    p.forcing = {"edm": 0, "moment": 1}[case.get("forcing", "edm")]
     kap = case.get("kappa", [0.0, 0.0])
     for k in range(2):
         p.kappa[k] = float(kap[k] if k < len(kap) else kap[0])

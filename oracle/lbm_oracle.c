@@ -70,7 +70,10 @@ typedef struct {
     int face_bc[6]; /* -x, +x, -y, +y, -z, +z */
     double face_rho[6][2];
     double kappa[2];  /* surface-tension adjustment (Section 2.3, D2Q9 MRT only); 0 = off */
+    int forcing;      /* ORC_FORCE_EDM (Eq. edm) | ORC_FORCE_MOMENT (F_m inside Eq. mrt_surface) */
 } orc_params;
+
+enum { ORC_FORCE_EDM = 0, ORC_FORCE_MOMENT = 1 };
 
 typedef struct {
     orc_params p;
@@ -544,6 +547,7 @@ orc_sim* orc_create(const orc_params* p)
 {
     if (!p || (p->dim != 2 && p->dim != 3) || p->ncomp < 1 || p->ncomp > 2) return NULL;
     if (p->nx < 1 || p->ny < 1 || p->nz < 1 || (p->dim == 2 && p->nz != 1)) return NULL;
+    if (p->forcing != ORC_FORCE_EDM && p->forcing != ORC_FORCE_MOMENT) return NULL;
     orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
     s->p = *p;
     s->dims[0] = p->nx; s->dims[1] = p->ny; s->dims[2] = p->nz;
@@ -795,8 +799,10 @@ static void fields_and_force(orc_sim* s)
  *   Q = kappa (g_kk / 2) [ (1 - A) psi(x) sum_i G_i (psi(x + e_i) - psi(x)) e_i e_i
  *                          + (A / 2) sum_i G_i (psi(x + e_i)^2 - psi(x)^2) e_i e_i ],
  * G_i = w_i / c_s^2 the force weights. The factor g_kk / 2 is that of Li et al. (2013),
- * whose scheme the paper implements; with it the surface tension scales with 1 - kappa
- * as the paper states (pinned by the Laplace tests). Zero unless D2Q9, MRT, kappa != 0. */
+ * whose scheme the paper implements. Together with the moment-space forcing of the same
+ * equation (ORC_FORCE_MOMENT) the surface tension scales with 1 - kappa as the paper states
+ * (pinned by the Laplace tests); with EDM forcing the F F / rho stress of that scheme does
+ * not scale with kappa. Zero unless D2Q9, MRT, kappa != 0. */
 /* Q = (Qxx, Qyy, Qxy) at node n from the psi field psi [K][N] (Q as defined above) */
 void orc_surface_Q(const orc_sim* s, const double* psi, long n, int k, double* Qout)
 {
@@ -833,12 +839,58 @@ static void surface_source(const orc_sim* s, long n, int k, double* C)
     C[8] = -snu * Qxy;
 }
 
+/* Moment-space forcing, the F_m that Eq. mrt_surface places inside M^-1[...] with the
+ * relaxation (Section 2.3; the scheme of Li et al. 2013 that the paper implements for
+ * the surface-tension adjustment). It is the forcing of Guo et al. (2002) written in
+ * moment space:
+ *   v = u_eq + F / (2 rho)                         (equilibrium at the physical velocity)
+ *   S_i = w_i [ (e_i - v) / c_s^2 + (e_i . v) e_i / c_s^4 ] . F
+ *   m* = m - S (m - m^eq(rho, v)) + (I - S/2) M S_i + C,     f* = M^-1 m*
+ * BGK is the case S = I / tau:  f* = f - (f - f^eq(rho, v)) / tau + (1 - 1/(2 tau)) S_i. */
+static void collide_node_moment_forcing(const orc_sim* s, const double* fin, double rho, const double* ueq,
+                                        const double* dU, int k, const double* Cm, double* fout)
+{
+    int Q = s->Q;
+    double v[3], F[3];
+    for (int a = 0; a < 3; ++a) { v[a] = ueq[a] + 0.5 * dU[a]; F[a] = rho * dU[a]; }
+    double neq[ORC_MAXQ], Si[ORC_MAXQ];
+    for (int i = 0; i < Q; ++i) {
+        neq[i] = fin[i] - feq(s, i, rho, v);
+        double ev = s->e[i][0] * v[0] + s->e[i][1] * v[1] + s->e[i][2] * v[2];
+        double acc = 0.0;
+        for (int a = 0; a < 3; ++a) acc += ((s->e[i][a] - v[a]) / CS2 + ev * s->e[i][a] / (CS2 * CS2)) * F[a];
+        Si[i] = s->w[i] * acc;
+    }
+    if (s->p.collision == ORC_BGK) {
+        double tau = s->p.tau[k];
+        for (int i = 0; i < Q; ++i) fout[i] = fin[i] - neq[i] / tau + (1.0 - 0.5 / tau) * Si[i];
+        return;
+    }
+    double m[ORC_MAXQ];
+    for (int a = 0; a < Q; ++a) {
+        double mn = 0.0, ms = 0.0;
+        for (int i = 0; i < Q; ++i) { mn += s->M[a][i] * neq[i]; ms += s->M[a][i] * Si[i]; }
+        double sa = s->rates[k][a];
+        /* m* - m = -s_a m_neq + (1 - s_a / 2) (M S)_a + C_a */
+        m[a] = -sa * mn + (1.0 - 0.5 * sa) * ms + (Cm ? Cm[a] : 0.0);
+    }
+    for (int i = 0; i < Q; ++i) {
+        double acc = 0.0;
+        for (int a = 0; a < Q; ++a) acc += s->Minv[i][a] * m[a];
+        fout[i] = fin[i] + acc;
+    }
+}
+
 /* (5)+(6) collision of one node, one component.
  * fin: Q post-stream populations; u_eq: equilibrium velocity; dU = F/rho;
  * Cm: moment-space source (MRT, may be NULL). */
 static void collide_node(const orc_sim* s, const double* fin, double rho, const double* ueq,
                          const double* dU, int k, const double* Cm, double* fout)
 {
+    if (s->p.forcing == ORC_FORCE_MOMENT) {
+        collide_node_moment_forcing(s, fin, rho, ueq, dU, k, Cm, fout);
+        return;
+    }
     int Q = s->Q;
     double fe[ORC_MAXQ], neq[ORC_MAXQ];
     for (int i = 0; i < Q; ++i) { fe[i] = feq(s, i, rho, ueq); neq[i] = fin[i] - fe[i]; }

@@ -73,6 +73,7 @@ struct Params {
     T accel[2][3];
     T rho_ref[2];        // 16-bit population storage holds f_i - w_i rho_ref[k] (0 otherwise)
     T kappa_g2[2];       // kappa g_kk / 2 of the surface-tension source (D2Q9 MRT; 0 = off)
+    int forcing_moment;  // 1: moment-space forcing of Eq. mrt_surface (D2Q9), 0: EDM (Eq. edm)
     T bc_rho[2][2];      // [x side][component]
 };
 

@@ -1007,8 +1007,23 @@ LBM_HD void collide(const Params<T>& P, int k, T (&f)[L::Q], T rho, const T (&u)
     }
     if (COLL == COLL_BGK) {
         const T om = P.omega[k];
+        if (L::D == 2 && P.forcing_moment) {
+            // moment-space forcing: the EDM update minus omega times the quadratic part of
+            // f^eq at du / 2, w_i rho (4.5 (e.du / 2)^2 - 1.5 |du / 2|^2)
+            const T duu = du[0] * du[0] + du[1] * du[1] + du[2] * du[2];
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) f[i] = f[i] + fma(-om, neq[i], edm_term<L, T>(i, rho, u, du));
+            for (int i = 0; i < L::Q; ++i) {
+                T edu = T(0);
+                if (L::ex(i)) edu += L::ex(i) > 0 ? du[0] : -du[0];
+                if (L::ey(i)) edu += L::ey(i) > 0 ? du[1] : -du[1];
+                if (L::ez(i)) edu += L::ez(i) > 0 ? du[2] : -du[2];
+                const T q = T(L::w(i)) * rho * fma(T(1.125) * edu, edu, T(-0.375) * duu);
+                f[i] = f[i] + fma(-om, neq[i] + q, edm_term<L, T>(i, rho, u, du));
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) f[i] = f[i] + fma(-om, neq[i], edm_term<L, T>(i, rho, u, du));
+        }
     } else {
         // Moment transforms through opposite pairs (i, opp(i)): moments even under
         // e -> -e see f_0 and the pair sums, odd moments the pair differences, which
@@ -1024,15 +1039,19 @@ LBM_HD void collide(const Params<T>& P, int k, T (&f)[L::Q], T rho, const T (&u)
             pd[p] = neq[i] - neq[o];
         });
         // EDM shift in moment space (velocity products as fused multiply-adds)
-        T dq[6];
+        T dq[6], dd[6];
         {
             const T up[3] = {u[0] + du[0], u[1] + du[1], u[2] + du[2]};
             int q = 0;
 #pragma unroll
             for (int d = 0; d < 3; ++d)
 #pragma unroll
-                for (int dp = d; dp < 3; ++dp) dq[q++] = fma(u[d], du[dp], du[d] * up[dp]);
+                for (int dp = d; dp < 3; ++dp) {
+                    dd[q] = T(0.25) * du[d] * du[dp];
+                    dq[q++] = fma(u[d], du[dp], du[d] * up[dp]);
+                }
         }
+        const bool fmom = L::D == 2 && P.forcing_moment;
         T m[L::Q];
         static_for<L::Q>([&](auto ac) {
             constexpr int a = decltype(ac)::value;
@@ -1077,6 +1096,19 @@ LBM_HD void collide(const Params<T>& P, int k, T (&f)[L::Q], T rho, const T (&u)
                 }
                 const T s = L::stress(a) ? P.omega[k] : P.rates[k][a];
                 const T cm = Cm ? Cm[a] : T(0);
+                if (fmom) {
+                    // moment-space forcing = EDM - S (moments of rho du du / 4): the relaxed
+                    // part of the second-order equilibrium shift
+                    T dg = T(0);
+                    static_for<6>([&](auto qc) {
+                        constexpr int q = decltype(qc)::value;
+                        constexpr int d = q < 3 ? 0 : (q < 5 ? 1 : 2);
+                        constexpr int dp = q < 3 ? q : (q < 5 ? q - 2 : 2);
+                        constexpr double c = (d < L::D && dp < L::D) ? edm_B<L>(a, d, dp) : 0.0;
+                        if constexpr (c != 0.0) dg = fma(T(c), dd[q], dg);
+                    });
+                    acc = fma(dg, rho, acc);
+                }
                 m[a] = (fma(-s, acc, dm) + cm) * T(inv_norm);
             }
         });

@@ -209,6 +209,8 @@ lbm_status validate(const lbm_params* p)
         if (!fin(p->kappa[k])) return LBM_ERR_INVALID_ARG;
         if (p->kappa[k] != 0.0 && (p->lattice != LBM_D2Q9 || p->collision != LBM_MRT)) return LBM_ERR_INVALID_ARG;
     }
+    if (p->forcing != LBM_FORCING_EDM && p->forcing != LBM_FORCING_MOMENT) return LBM_ERR_INVALID_ARG;
+    if (p->forcing == LBM_FORCING_MOMENT && p->lattice != LBM_D2Q9) return LBM_ERR_INVALID_ARG;
     if (p->schedule != LBM_SCHEDULE_AUTO && p->schedule != LBM_SCHEDULE_TWO_PASS &&
         p->schedule != LBM_SCHEDULE_SINGLE_PASS && p->schedule != LBM_SCHEDULE_SLAB_OVERLAP)
         return LBM_ERR_INVALID_ARG;
@@ -327,6 +329,7 @@ void fill_params(const lbm_ctx* c, Params<T>& P)
         P.rho_ref[k] = (p->real == LBM_FP16S || p->real == LBM_BF16S) ? (T)p->rho_ref[kk] : T(0);
         P.kappa_g2[k] = (T)(p->kappa[kk] * 0.5 * p->g[kk][kk]);
     }
+    P.forcing_moment = p->forcing == LBM_FORCING_MOMENT;
 }
 
 template <typename T>

@@ -302,16 +302,32 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity)
     return done != 0;
 }
 
-// wait for the completion of phase `parity`; false (and the error flag) after ~2 s
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity)
+// wait for the completion of phase `parity`; false (and the error flag) after `limit`
+// SM clock cycles (~2 s by default)
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit = kWaitCycles)
 {
     const long long t0 = clock64();
     while (!mbar_test(bar, parity))
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > limit) {
             atomicOr(&g_tc_error, 1u);
             return false;
         }
     return true;
+}
+
+// Failure-detection check of the bounded wait: one thread initialises an mbarrier that
+// expects one arrival, never arrives on it and waits for its first phase with the given
+// limit. No tensor memory is allocated and no MMA or copy is in flight, so giving up is
+// the only way out and nothing is left behind. The outcome goes to g_wait_result.
+__device__ int g_wait_result;
+
+__global__ void k_wait_selftest(long long limit)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t b = smem_addr(&bar);
+    mbar_init(b);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    g_wait_result = mbar_wait(b, 0, limit) ? 1 : 0;
 }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -951,6 +967,22 @@ lbm_status lbm_nn_conv3d_tc_grad_weight(const float* x, int cin, const float* gy
 {
     if (!x || !gy || !gw || !scratch || cin < 1 || cout < 1 || d < 1 || h < 1 || w < 1) return LBM_ERR_INVALID_ARG;
     return gw_tc(x, cin, gy, cout, d, h, w, gw, gb, accumulate, scratch, (cudaStream_t)stream);
+}
+
+lbm_status lbm_nn_wait_selftest(long long limit_cycles, int* completed, void* stream)
+{
+    if (!completed || limit_cycles < 1 || limit_cycles > kWaitCycles) return LBM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int v = -1;
+    if (cudaMemcpyToSymbolAsync(g_wait_result, &v, sizeof v, 0, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    k_wait_selftest<<<1, 1, 0, st>>>(limit_cycles);
+    if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
+    if (cudaMemcpyFromSymbolAsync(&v, g_wait_result, sizeof v, 0, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    *completed = v;
+    return LBM_OK;
 }
 
 lbm_status lbm_nn_tc_error(int* flag)

@@ -1,15 +1,16 @@
 // lbm_mass_noalloc: total mass per component with no memory allocation at all.
 //
-// Some callers cannot allocate device memory: code that runs while a CUDA graph is
-// being captured, host processes that hand the GPU to a framework owning every
-// allocation, or callers whose memory pool is exhausted by the lattice itself. This
-// entry point computes the same mass sums as lbm_diagnostics from populations the
-// caller already holds, and keeps its scratch (the per-block FP64 partial sums of
-// the two-stage reduction) in a file-scope device array instead of a caller
-// workspace. That array lives on every GPU that loads the library until the
-// process exits.
+// Some callers cannot allocate device memory: host processes that hand the GPU to a
+// framework owning every allocation, or callers whose memory pool is exhausted by the
+// lattice itself. This entry point computes the same mass sums as lbm_diagnostics
+// from populations the caller already holds, and keeps its scratch (the per-block FP64
+// partial sums of the two-stage reduction) in a file-scope device array instead of a
+// caller workspace. That array lives on every GPU that loads the library until the
+// process exits. The call copies the totals to host memory and synchronises its
+// stream, so it cannot run on a stream that is being captured into a CUDA graph.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "lbm.h"
@@ -28,8 +29,10 @@ static_assert(LBM_NOALLOC_MAX_NODES % kNodesPerBlock == 0, "max nodes must fill 
 static __device__ __align__(256) double g_mass_scratch[kMaxBlocks * 2 + 2];
 
 // Device address of g_mass_scratch per device ordinal (host code cannot use the
-// symbol itself: in host code its name stands for a host-side shadow object).
-void* g_scratch_ptr[kMaxDevices] = {};
+// symbol itself: in host code its name stands for a host-side shadow object). Atomic,
+// because host threads making their first call on a device may fill the same entry at
+// once (with the same value).
+std::atomic<void*> g_scratch_ptr[kMaxDevices] = {};
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_mass_partials(const T* __restrict__ f, int K, int Q, long long N,
@@ -86,12 +89,12 @@ lbm_status scratch_of_current_device(double** out)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return LBM_ERR_INVALID_ARG;
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
+    void* p = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
         if (cudaGetSymbolAddress(&p, g_mass_scratch) != cudaSuccess || !p) return LBM_ERR_CUDA;
-        g_scratch_ptr[dev] = p;
+        g_scratch_ptr[dev].store(p, std::memory_order_release);
     }
-    *out = (double*)g_scratch_ptr[dev];
+    *out = (double*)p;
     return LBM_OK;
 }
 

@@ -56,6 +56,7 @@ class lbm_params(C.Structure):
         ("schedule", C.c_int),
         ("rho_ref", C.c_double * 2),
         ("kappa", C.c_double * 2),
+        ("forcing", C.c_int),
     ]
 
 
@@ -247,6 +248,7 @@ def params_from_case(case):
     for k in range(2):
         p.rho_ref[k] = float(rr[k] if k < len(rr) else rr[0])
         p.kappa[k] = float(kap[k] if k < len(kap) else kap[0])
+    p.forcing = {"edm": 0, "moment": 1}[case.get("forcing", "edm")]
     p.collision = LBM_MRT if case.get("collision", "BGK") == "MRT" else LBM_BGK
     p.velocity = LBM_UEQ_COMMON if case.get("velocity", "component") == "common" else LBM_UEQ_COMPONENT
     p.tau[:] = _two(case.get("tau"), 1.0)

@@ -8,7 +8,7 @@ from .lbm import LbmError, library as _lbm_library
 EXPORTS = ["lbm_nn_conv3d", "lbm_nn_conv3d_grad_input", "lbm_nn_conv3d_grad_weight", "lbm_nn_axpy", "lbm_nn_relu_grad",
            "lbm_nn_avg_pool2", "lbm_nn_avg_pool2_grad", "lbm_nn_up2", "lbm_nn_up2_grad", "lbm_nn_rel_loss",
            "lbm_nn_adam", "lbm_nn_conv3d_tc", "lbm_nn_conv3d_tc_grad_input", "lbm_nn_conv3d_tc_grad_weight",
-           "lbm_nn_tc_error"]
+           "lbm_nn_tc_error", "lbm_nn_wait_selftest"]
 GW_SEGMENTS = 64          # LBM_NN_GW_SEGMENTS: scratch of conv3d_grad_weight, 64 cout cin 28 floats
 GW_TC_SEGMENTS = 512      # LBM_NN_GW_TC_SEGMENTS: scratch of the tensor-core form, 512 cout (27 cin + 1) floats
 
@@ -39,6 +39,7 @@ def library():
         L.lbm_nn_conv3d_tc_grad_input.argtypes = L.lbm_nn_conv3d_grad_input.argtypes
         L.lbm_nn_conv3d_tc_grad_weight.argtypes = L.lbm_nn_conv3d_grad_weight.argtypes
         L.lbm_nn_tc_error.argtypes = [C.POINTER(C.c_int)]
+        L.lbm_nn_wait_selftest.argtypes = [C.c_longlong, C.POINTER(C.c_int), vp]
         for n in EXPORTS:
             getattr(L, n).restype = C.c_int
         _ready = True
@@ -88,6 +89,13 @@ def tc_error():
     flag = C.c_int(0)
     _check(library().lbm_nn_tc_error(C.byref(flag)), "lbm_nn_tc_error")
     return flag.value
+
+
+def wait_selftest(limit_cycles, stream=None):
+    """1 if a bounded wait on a barrier that nothing arrives on completed, 0 if it gave up."""
+    done = C.c_int(-1)
+    _check(library().lbm_nn_wait_selftest(int(limit_cycles), C.byref(done), _st(stream)), "lbm_nn_wait_selftest")
+    return done.value
 
 
 def axpy(y, x, a=1.0, stream=None):

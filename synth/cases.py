@@ -23,6 +23,9 @@ Keys:
   accel        per component body acceleration (3)
   bc           6 faces (-x, +x, -y, +y, -z, +z): "periodic" | "wall" | "pressure"
   bc_rho       6 x ncomp face densities (pressure faces)
+  kappa        per component surface-tension adjustment (D2Q9 MRT; 0 = off)
+  forcing      "edm" (Eq. edm, the default) | "moment" (the moment-space forcing that
+               Eq. mrt_surface places inside M^-1[...]; D2Q9)
 """
 import numpy as np
 
@@ -58,6 +61,10 @@ COEX = {
 # (flat-interface coexistence equal to the Maxwell pair within 0.1 %), found by
 # bisection on the vapour density of a flat liquid slab (D2Q9, BGK, tau = 1).
 A_STAR = {("CS", 0.7): -0.276, ("CS", 0.8): -0.275, ("PR", 0.6): -0.233, ("PR", 0.8): -0.249}
+# The same bisection with the moment-space forcing of the surface-tension collision
+# (forcing = "moment", D2Q9 MRT with the Lallemand-Luo rates, tau = 1): that forcing lacks
+# EDM's F F / rho stress, so mechanical stability needs a stronger Zhang-Chen share.
+A_STAR_MOMENT = {("CS", 0.7): -0.886}
 
 # Peng-Robinson at T = 0.6 Tc (density ratio 853): the liquid sits close to the
 # repulsive pole 1/b, so the EOS is stiff and droplets blow up with alpha = 1.

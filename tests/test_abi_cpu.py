@@ -31,7 +31,7 @@ def test_exports_every_declared_symbol(lib):
         assert hasattr(lib, n), n
     assert sorted(lbm.EXPORTS) == names
     nn_names = _declared("lbm_nn.h")
-    assert len(nn_names) == 15
+    assert len(nn_names) == 16
     for n in nn_names:
         assert hasattr(lib, n), n
     assert sorted(nn.EXPORTS) == nn_names
@@ -51,6 +51,10 @@ def test_network_entry_points_validate_arguments_on_the_host(lib):
     assert L.lbm_nn_conv3d_tc_grad_input(fake, 300, 4, 4, 4, fake, 8, fake, fake, None) == 1
     assert L.lbm_nn_conv3d_tc_grad_weight(fake, 8, fake, 300, 4, 4, 4, fake, None, 0, fake, None) == 1
     assert L.lbm_nn_tc_error(None) == 1
+    done = C.c_int(-1)
+    assert L.lbm_nn_wait_selftest(0, C.byref(done), None) == 1               # limit out of range
+    assert L.lbm_nn_wait_selftest(5_000_000_000, C.byref(done), None) == 1
+    assert L.lbm_nn_wait_selftest(1000, None, None) == 1
 
 
 def test_status_strings(lib):
@@ -99,6 +103,7 @@ def test_workspace_size_layout(lib):
     dict(shape=(2048, 1024, 1024)),            # 2^31 nodes: node indices are 32-bit
     dict(real="f16s", rho_ref=[float("nan"), 1.0]),
     dict(kappa=[0.5, 0.5]),                    # surface-tension source: D2Q9 MRT only
+    dict(forcing="moment"),                    # moment-space forcing: D2Q9 only
 ])
 def test_rejects_invalid_parameters(lib, bad):
     from paper_2506_17713_gb300 import lbm

@@ -284,3 +284,22 @@ def test_training_reduces_the_loss():
     us = [np.stack([(1 - s) * 2e-4, (1 - s) * 1e-5, 0 * s, 1e-4 * (1 - s)]).astype(np.float32) for s in solids]
     hist = train(net, solids, us, epochs=30, batch=2, lr=3e-3)
     assert hist[-1] < 0.5 * hist[0]
+
+
+def test_bounded_wait_gives_up_and_sets_the_error_flag():
+    # failure detection of the tensor-core kernels, made to fire without a fault: a wait on
+    # an mbarrier that nothing arrives on gives up after the limit (2e6 cycles, about a
+    # millisecond), reports it, and sets the flag lbm_nn_tc_error reads and clears
+    from paper_2506_17713_gb300 import nn
+    nn.tc_error()
+    assert nn.wait_selftest(2_000_000) == 0
+    assert nn.tc_error() == 1
+    assert nn.tc_error() == 0
+    # the context stays usable: a tensor-core convolution still runs and sets no flag
+    import torch
+    x = torch.rand((4, 8, 8, 8), device="cuda")
+    w = torch.rand((16, 4, 27), device="cuda")
+    y = torch.empty((16, 8, 8, 8), device="cuda")
+    nn.conv3d(x, w, None, False, y, tc=True)
+    torch.cuda.synchronize()
+    assert torch.isfinite(y).all() and nn.tc_error() == 0

@@ -333,6 +333,52 @@ def test_virtual_density_special_cases():
         assert np.allclose(psi[b], rho[b], atol=1e-14)   # psi = rho at solids too
 
 
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19"])
+def test_virtual_density_weighting_on_a_density_quadratic_along_the_wall(lattice):
+    # Eq. improved_virtual_density: rho_ave is the lattice-weighted mean over the fluid
+    # neighbours of a solid node. On a flat wall the fluid neighbours of a wall node x_s are
+    # the first fluid layer at x_s + n, x_s + n +- t (t along the wall), with weights
+    # w(1) for the normal link and w(2) for the diagonals, so
+    #   D2Q9:  (4 rho(0) + rho(-1) + rho(+1)) / 6            = rho + rho'' / 6,
+    #   D3Q19: (2 rho(0) + the four in-plane neighbours) / 6 = rho + (rho_xx + rho_yy) / 6
+    # for a density quadratic along the wall (an unweighted mean gives / 3; solid neighbours
+    # in the denominator scale it by 1/4 or 1/3). rho_s = phi rho_ave - drho on top of it.
+    if lattice == "D2Q9":
+        shape, nz = (14, 9, 1), 1
+    else:
+        shape, nz = (12, 11, 7), 7
+    nx, ny = shape[0], shape[1]
+    # walls two layers thick: y = 0, 1 in 2-D, z = 0, 1 in 3-D (periodic, so the far side is fluid)
+    solid = np.zeros((nz, ny, nx), dtype=np.uint8)
+    if lattice == "D2Q9":
+        solid[0, 0:2, :] = 1
+    else:
+        solid[0:2, :, :] = 1
+    X, Y = np.meshgrid(np.arange(nx, dtype=float) - nx / 2, np.arange(ny, dtype=float) - ny / 2)
+    rho = 0.5 + 0.3 * random_field(shape, 0.0, 1.0, 17)           # arbitrary elsewhere
+    cxx, cyy, cxy, bx, by = 2e-3, -1.2e-3, 7e-4, 0.01, -0.02
+    if lattice == "D2Q9":
+        xs = np.arange(nx, dtype=float) - nx / 2
+        layer = 0.8 + bx * xs + 0.5 * cxx * xs * xs
+        rho[0, 2, :] = layer
+        expect_inner = layer + cxx / 6.0
+        sl = (0, 1, slice(1, nx - 1))
+        expect = expect_inner[1:nx - 1]
+    else:
+        layer = 0.8 + bx * X + by * Y + 0.5 * (cxx * X * X + 2 * cxy * X * Y + cyy * Y * Y)
+        rho[2] = layer
+        sl = (1, slice(1, ny - 1), slice(1, nx - 1))
+        expect = (layer + (cxx + cyy) / 6.0)[1:ny - 1, 1:nx - 1]
+    for phi, drho in [(1.0, 0.0), (1.25, 0.0), (1.0, 0.07)]:
+        case = cases.base_case(lattice, shape, psi=["rho"], wet_phi=[phi, phi], wet_drho=[drho, drho],
+                               rho_lo=[0.0, 0.0], rho_hi=[10.0, 10.0])
+        s = oracle.OracleSim(case)
+        s.set_geometry(solid)
+        s.init_fields(0, rho)
+        _, rv = s.psi(0)
+        assert np.allclose(rv[sl], phi * expect - drho, rtol=1e-13, atol=1e-14)
+
+
 def test_neutral_wetting_flat_wall_force_vanishes_normal():
     # phi = 1, drho = 0 on a uniform fluid: solids mirror the fluid density, so
     # the interaction force at wall-adjacent fluid nodes vanishes (90 degrees)

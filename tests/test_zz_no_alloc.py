@@ -30,6 +30,10 @@ def _lattice(variant):
         case, init = cases.droplets_3d_pr(shape=(48, 40, 36), count=1, rmin=10.0, rmax=10.0, seed=5)
         lat = Lattice(case)
         lat.init_fields(0, init["rho"][0])
+    elif variant == "d2q9_cs_f64":
+        case, init = cases.droplet_2d_cs(n=64, radius=14.0)
+        lat = Lattice(case)
+        lat.init_fields(0, init["rho"][0])
     else:
         shape = (23, 19, 17)
         case = cases.base_case("D3Q19", shape, ncomp=2, psi=["rho", "rho"], velocity="common", real="f64",
@@ -42,7 +46,7 @@ def _lattice(variant):
     return lat
 
 
-@pytest.mark.parametrize("variant", ["pr_f32", "two_comp_f64_solids"])
+@pytest.mark.parametrize("variant", ["pr_f32", "d2q9_cs_f64", "two_comp_f64_solids"])
 def test_mass_noalloc_matches_diagnostics_twice(variant):
     import torch
     from paper_2506_17713_gb300 import lbm
@@ -66,3 +70,13 @@ def test_mass_noalloc_rejects_oversized_lattice():
     mass = (C.c_double * 2)()
     # rejected before any device work, so a dummy pointer is never touched
     assert lbm.library().lbm_mass_noalloc(C.byref(p), C.c_void_p(256), mass, None) == 1
+
+
+def test_mass_noalloc_rejects_16bit_storage():
+    # the entry point reads populations as FP32 or FP64; shifted 16-bit buffers are refused
+    # on the host, before any device work, so the dummy pointer is never touched
+    from paper_2506_17713_gb300 import lbm
+    for real in ("f16s", "bf16s"):
+        p = lbm.params_from_case(cases.base_case("D3Q19", (16, 16, 16), real=real))
+        mass = (C.c_double * 2)()
+        assert lbm.library().lbm_mass_noalloc(C.byref(p), C.c_void_p(256), mass, None) == 1
