@@ -38,9 +38,12 @@ WORKLOADS = {
               "adjoint and weight gradient, BF16 tensor cores vs FP32 CUDA cores",
     "warmstart_errors": "which errors of a warm start cost relaxation steps: the warm-start samples started from "
                         "their converged field with a scaled magnitude, white or smooth velocity noise, or density "
-                        "noise",
+                        "noise, and from the run's own early field rescaled to the exact flux",
     "batch64": "64 D3Q19 sphere-pack drainage samples, box edges U[64,192] (seed 2024), overlapping spheres "
                "r U[8,12] to porosity 0.38, PR T=0.8Tc MRT FP32, wetting solids, per-sample inlet pressure step",
+    "drainage400": "the porous400 drainage as configured: non-wetting phase injected through the constant-density "
+                   "inlet into the wetting-saturated 400^3 GRF medium (45-degree wetting), 20000 steps, FP32 "
+                   "storage and FP16 / BF16 shifted storage; saturation history and breakthrough",
 }
 
 
@@ -512,10 +515,16 @@ def run_warmstart_errors(args):
         r["velocity_plus_30pct_smooth_noise_exact_density"] = ws.relax(n, solid, up + sm, rho0=rp)[0]
         dn = 0.01 * (rp - 1.0).std() * rng.standard_normal(rp.shape)
         r["exact_velocity_density_plus_1pct_noise"] = ws.relax(n, solid, up, rho0=rp + dn)[0]
+        # the run from rest stopped after m steps, its departure from rest scaled by the exact
+        # q_inf / q(m) (a perfect magnitude prediction applied to the LBM's own early field)
+        q_inf = float(up[0][fl].mean())
+        for m in (200, 800):
+            r["rest_%d_steps_then_exact_flux_rescale" % m], r["flux_ratio_at_%d" % m] = \
+                ws.relax_scaled_early_field(n, solid, m, q_inf)
         rows.append(r)
     if rank != 0:
         return
-    keys = [k for k in rows[0] if k != "porosity"]
+    keys = [k for k in rows[0] if k != "porosity" and not k.startswith("flux_ratio")]
     print(json.dumps({
         "metric": "steps to residual <= 1e-6 by start (mean over samples)", "value": float(np.mean([r["rest"] for r in rows])),
         "unit": "steps", "n_gpus": world, "steps": int(sum(sum(r[k] for k in keys) for r in rows)), "warmup": 0,
@@ -607,6 +616,92 @@ def run_warmstart(args):
                          "warm_total_incl_inference": round(float(r[:, 3].sum()), 3)},
         "permeability": {"max_rel_diff_warm_vs_plain": float(kerr.max()), "plain_mean": float(r[:, 4].mean())},
         "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_drainage(args):
+    """Drainage of the two-component porous workload as configured (400^3 GRF medium,
+    porosity 0.15, corr. length 6, 8-lu buffers, wetting phase at 45 degrees through the
+    calibrated virtual density, immiscible fluids): the non-wetting phase enters through
+    the constant-density inlet. The same run goes once per population storage (FP32, FP16
+    and BF16 deviations, FP32 compute). Every `drain_every` steps the non-wetting
+    saturation S_nw (fluid nodes between the buffers where the non-wetting density exceeds
+    the wetting one) is taken on the device; breakthrough is the first sample with
+    non-wetting nodes in the last plane before the outlet buffer. Reported: the histories,
+    MLUPS of the stepping alone (CUDA events; the samples excluded) and the 16-bit runs'
+    deviation from FP32 (largest |S - S_FP32| over the samples, and the fraction of fluid
+    nodes whose phase differs at the end)."""
+    import torch
+    from paper_2506_17713_gb300 import Lattice
+    from synth import cases
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    m = 400 if args.n == 256 else args.n
+    case0, init = cases.porous_two_component(shape=(m, m, m))
+    solid = init["solid"]
+    buf = cases.POROUS_BUFFER
+    fluid = torch.from_numpy(solid == 0).cuda()
+    core = fluid.clone()
+    core[:, :, :buf] = False
+    core[:, :, m - buf:] = False
+    last = fluid[:, :, m - buf - 1]
+    n_core = int(core.sum())
+    K = 2
+    N = m ** 3
+    steps, every = args.drain_steps, args.drain_every
+    runs, final = {}, {}
+    for real in ("f32", "f16s", "bf16s"):
+        case = dict(case0, real=real)
+        if real != "f32":
+            # each component's reference: the density it has in most of the domain at the start
+            # (wetting: the major value, non-wetting: the dissolved one), so that most stored
+            # deviations are small
+            case["rho_ref"] = list(args.drain_rho_ref)
+        lat = Lattice(case)
+        lat.set_geometry(solid)
+        for k, r in enumerate(init["rho"]):
+            lat.init_fields(k, r)
+        hist, bt, secs = [], None, 0.0
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        for t in range(every, steps + 1, every):
+            ev0.record(lat.stream)
+            lat.step(every)
+            ev1.record(lat.stream)
+            torch.cuda.synchronize()
+            secs += ev0.elapsed_time(ev1) / 1e3
+            rw, _ = lat.macroscopic(0)
+            rn, _ = lat.macroscopic(1)
+            nw = rn > rw
+            s = float((nw & core).sum()) / n_core
+            hist.append([t, round(s, 6)])
+            if bt is None and bool((nw[:, :, m - buf - 1] & last).any()):
+                bt = t
+        m0, _ = lat.diagnostics()
+        runs[real] = {"saturation": hist, "breakthrough_step": bt, "mlups": round(K * N * steps / secs / 1e6, 1),
+                      "mass": [float(x) for x in m0]}
+        final[real] = nw.clone()
+        lat.close()
+        del lat
+        torch.cuda.empty_cache()
+    for real in ("f16s", "bf16s"):
+        ds = max(abs(a[1] - b[1]) for a, b in zip(runs[real]["saturation"], runs["f32"]["saturation"]))
+        runs[real]["max_abs_saturation_diff_vs_f32"] = round(ds, 6)
+        runs[real]["phase_mismatch_fraction_vs_f32"] = round(float((final[real] != final["f32"])[fluid].float().mean()), 6)
+    if rank != 0:
+        return
+    line = {
+        "metric": "two-component porous drainage: non-wetting saturation after %d steps" % steps,
+        "value": runs["f32"]["saturation"][-1][1], "unit": "fraction of pore nodes", "higher_is_better": True,
+        "n_gpus": world, "steps": steps, "warmup": 0, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS["drainage400"], "shape": [m, m, m], "fluid_nodes": int(fluid.sum()),
+                   "core_nodes": n_core, "sample_every": every,
+                   "wet_phi": case0["wet_phi"], "g12": case0["g"][0][1], "tau": case0["tau"],
+                   "inlet_rho": case0["bc_rho"][0], "outlet_rho": case0["bc_rho"][1],
+                   "rho_ref_16bit": list(args.drain_rho_ref)},
+        "runs": runs,
     }
     print(json.dumps(line), flush=True)
 
@@ -800,6 +895,10 @@ def main():
     ap.add_argument("--batch-edge-hi", type=int, default=192)
     ap.add_argument("--batch-seq-steps", type=int, default=50,
                     help="steps of the sequential comparison (batch64)")
+    ap.add_argument("--drain-steps", type=int, default=20000, help="drainage400: steps per storage mode")
+    ap.add_argument("--drain-every", type=int, default=1000, help="drainage400: steps between saturation samples")
+    ap.add_argument("--drain-rho-ref", type=float, nargs=2, default=[1.07, 0.008],
+                    help="drainage400: 16-bit reference densities of the wetting and non-wetting components")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -813,6 +912,8 @@ def main():
         run_warmstart_errors(args)
     elif args.workload == "conv3d":
         run_conv3d(args)
+    elif args.workload == "drainage400":
+        run_drainage(args)
     else:
         run_ours(args)
 

@@ -158,10 +158,15 @@ typedef struct lbm_ctx lbm_ctx;
  * Returns LBM_ERR_INVALID_ARG for invalid parameters. */
 lbm_status lbm_workspace_size(const lbm_params* p, size_t* bytes);
 
-/* Create a context on the current CUDA device. d_workspace: device pointer, 256-byte
+/* Create a context on the current CUDA device: the lattice, EOS, wetting and boundary
+ * parameters of one problem (Section 2: Eqs. lbe, collision_model, eos_potential,
+ * software_ff_force_mcmp, improved_virtual_density; the critical temperature of each
+ * EOS is found from its definition, Section 3.1). d_workspace: device pointer, 256-byte
  * aligned, at least lbm_workspace_size() bytes, owned by the caller; stream: the
  * caller's cudaStream_t. On success *out receives the context (host memory owned by
- * the library, freed by lbm_destroy). The geometry starts all-fluid. */
+ * the library, freed by lbm_destroy). The geometry starts all-fluid. Returns
+ * LBM_ERR_INVALID_ARG for invalid parameters or pointers, LBM_ERR_WORKSPACE for a
+ * missing, misaligned or small workspace, LBM_ERR_CUDA if the device set-up fails. */
 lbm_status lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void* stream,
                       lbm_ctx** out);
 
@@ -187,16 +192,21 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
  * rho: [N], u: [D][N]; either may be NULL; solids give 0. */
 lbm_status lbm_macroscopic(lbm_ctx* ctx, int comp, void* rho, void* u, int where);
 
-/* Total mass sum_x rho^k and momentum sum_x (j^k + F^k/2) per component, summed in
- * FP64 in a fixed order (deterministic). mass: [ncomp]; momentum: [ncomp][3].
+/* Total mass sum_x rho^k and momentum sum_x (j^k + F^k/2) per component (Eq. macroeq_mcp
+ * and the velocity after Eq. edm; mass is conserved exactly by the step, Section 3.1),
+ * summed in FP64 in a fixed order (deterministic). mass: [ncomp]; momentum: [ncomp][3].
  * residual (may be NULL): ||u - u_prev||_2 / ||u||_2 of the mixture velocity over fluid
  * nodes, u_prev being the velocity at the previous call that asked for a residual
- * (1.0 on the first such call). Synchronises; reports LBM_ERR_UNSTABLE if a step met a
- * non-finite or non-positive density. */
+ * (1.0 on the first such call). The paper runs its steady cases to a steady state
+ * (Sections 3.1 and 3.4.1) without naming a criterion; this residual, taken every k steps
+ * and compared with a threshold such as 1e-6, is the reading used here.
+ * Synchronises; reports LBM_ERR_UNSTABLE if a step met a non-finite or non-positive
+ * density. */
 lbm_status lbm_diagnostics(lbm_ctx* ctx, double* mass, double* momentum, double* residual);
 
 /* Post-stream populations of component comp, [Q][N] of the compute type (checkpoint /
- * inspection). lbm_set_populations restores them exactly (bit for bit), except for the
+ * inspection; the paper has no passage on checkpoints: this is the state f_i of
+ * Eq. lbe_steps after streaming). lbm_set_populations restores them exactly (bit for bit), except for the
  * populations that constant-density faces recompute. With 16-bit storage the values are
  * the stored deviations plus w_i rho_ref in FP32, and lbm_set_populations rounds
  * f_i - w_i rho_ref back to the storage type (the values lbm_get_populations returned

@@ -707,9 +707,11 @@ template <class L, typename T, int K, bool EXACT = true, class PsiAt>
 LBM_HD void interaction_force_at(const Params<T>& P, const PsiAt& psi_at, const T (&rho)[K], T (&F)[K][3])
 {
     T S[K][3], D[K][3], px[K];
+    bool mixA[K];   // two components: D^k only enters with A_k != 0 (A_k = 0: Shan-Chen alone)
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         px[k] = psi_at(k, 0, 0, 0);
+        mixA[k] = K == 1 || P.A[k] != T(0);
 #pragma unroll
         for (int d = 0; d < 3; ++d) S[k][d] = D[k][d] = T(0);
     }
@@ -722,10 +724,15 @@ LBM_HD void interaction_force_at(const Params<T>& P, const PsiAt& psi_at, const 
             const T p1 = psi_at(k, L::ex(i), L::ey(i), L::ez(i));
             const T p2 = psi_at(k, -L::ex(i), -L::ey(i), -L::ez(i));
             const T dh = c * (p1 - p2);                            // c <= 4: exact
-            const T dd = dh * ((p1 - px[k]) + (p2 - px[k]));       // 2 dpsi delta
-            if (L::ex(i)) { S[k][0] += L::ex(i) > 0 ? dh : -dh; D[k][0] += L::ex(i) > 0 ? dd : -dd; }
-            if (L::ey(i)) { S[k][1] += L::ey(i) > 0 ? dh : -dh; D[k][1] += L::ey(i) > 0 ? dd : -dd; }
-            if (L::ez(i)) { S[k][2] += L::ez(i) > 0 ? dh : -dh; D[k][2] += L::ez(i) > 0 ? dd : -dd; }
+            if (L::ex(i)) S[k][0] += L::ex(i) > 0 ? dh : -dh;
+            if (L::ey(i)) S[k][1] += L::ey(i) > 0 ? dh : -dh;
+            if (L::ez(i)) S[k][2] += L::ez(i) > 0 ? dh : -dh;
+            if (mixA[k]) {
+                const T dd = dh * ((p1 - px[k]) + (p2 - px[k]));   // 2 dpsi delta
+                if (L::ex(i)) D[k][0] += L::ex(i) > 0 ? dd : -dd;
+                if (L::ey(i)) D[k][1] += L::ey(i) > 0 ? dd : -dd;
+                if (L::ez(i)) D[k][2] += L::ez(i) > 0 ? dd : -dd;
+            }
         }
     }
     if constexpr (!EXACT) {
@@ -984,6 +991,52 @@ LBM_HD void collide_mrt_d3q19(const Params<T>& P, int k, T (&f)[19], T rho, cons
     }
 }
 
+// BGK collision with EDM forcing over opposite pairs (i, opp(i)). e.u, e.du and
+// e.(2u + du) change sign between the two directions of a pair, so the even parts of
+// f^eq and of the EDM term are formed once per pair and the odd parts once:
+//   f^eq_i = W (1 + P_s + P_a) + L,  P_s = 4.5 (e.u)^2 - 1.5 u.u,  P_a = 3 e.u,
+//   edm_i  = W (E_s + E_a),           E_s = 4.5 (e.(2u+du)) (e.du) - 1.5 (2u+du).du,  E_a = 3 e.du,
+// with the opposite direction taking -P_a, -E_a. W is w rho rounded and L its rounding
+// error plus w_lo rho, so neq = (f - W) - (W poly + L) keeps f - W exact, as in the
+// per-direction form, and f* = f + (edm - omega neq) lands one rounding on f.
+template <class L, typename T>
+LBM_HD void collide_bgk_pairs(const Params<T>& P, int k, T (&f)[L::Q], T rho, const T (&u)[3], const T (&du)[3])
+{
+    constexpr int NP = (L::Q - 1) / 2;
+    const T om = P.omega[k];
+    const T m15uu = T(-1.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const T s[3] = {fma(T(2), u[0], du[0]), fma(T(2), u[1], du[1]), fma(T(2), u[2], du[2])};
+    const T m15sdu = T(-1.5) * (s[0] * du[0] + s[1] * du[1] + s[2] * du[2]);
+    auto wsplit = [&](double w, T& W, T& Lw) {
+        const T wh = T(w), wl = T(w - (double)T(w));
+        const FF<T> wr = ff_two_prod(wh, rho);
+        W = wr.hi;
+        Lw = fma(wl, rho, wr.lo);
+    };
+    {
+        T W, Lw;
+        wsplit(L::w(0), W, Lw);
+        const T neq = (f[0] - W) - fma(W, m15uu, Lw);
+        f[0] = f[0] + fma(-om, neq, W * m15sdu);
+    }
+    static_for<NP>([&](auto pc) {
+        constexpr int i = pair_first<L>(decltype(pc)::value);
+        constexpr int o = L::opp(i);
+        T W, Lw;
+        wsplit(L::w(i), W, Lw);
+        T a = T(0), dl = T(0), sg = T(0);
+        if constexpr (L::ex(i) != 0) { a += L::ex(i) > 0 ? u[0] : -u[0]; dl += L::ex(i) > 0 ? du[0] : -du[0]; sg += L::ex(i) > 0 ? s[0] : -s[0]; }
+        if constexpr (L::ey(i) != 0) { a += L::ey(i) > 0 ? u[1] : -u[1]; dl += L::ey(i) > 0 ? du[1] : -du[1]; sg += L::ey(i) > 0 ? s[1] : -s[1]; }
+        if constexpr (L::ez(i) != 0) { a += L::ez(i) > 0 ? u[2] : -u[2]; dl += L::ez(i) > 0 ? du[2] : -du[2]; sg += L::ez(i) > 0 ? s[2] : -s[2]; }
+        const T Ps = fma(T(4.5) * a, a, m15uu), Pa = T(3) * a;
+        const T Es = fma(T(4.5) * sg, dl, m15sdu), Ea = T(3) * dl;
+        const T neq_i = (f[i] - W) - fma(W, Ps + Pa, Lw);
+        const T neq_o = (f[o] - W) - fma(W, Ps - Pa, Lw);
+        f[i] = f[i] + fma(-om, neq_i, W * (Es + Ea));
+        f[o] = f[o] + fma(-om, neq_o, W * (Es - Ea));
+    });
+}
+
 // Collision and EDM forcing of one component at one node. The update is formed
 // as f_i + (small correction) so that only one rounding lands on f_i. BGK adds
 // the EDM shift per direction; MRT adds it in moment space together with the
@@ -996,6 +1049,12 @@ LBM_HD void collide(const Params<T>& P, int k, T (&f)[L::Q], T rho, const T (&u)
     if constexpr (COLL != COLL_BGK && L::Q == 19) {
         collide_mrt_d3q19<T>(P, k, f, rho, u, du);
         return;
+    }
+    if constexpr (COLL == COLL_BGK) {
+        if (!(L::D == 2 && P.forcing_moment)) {
+            collide_bgk_pairs<L, T>(P, k, f, rho, u, du);
+            return;
+        }
     }
     const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     T neq[L::Q];
@@ -1226,13 +1285,37 @@ __device__ __forceinline__ void collide_node(const KArgs<T>& a, const Node& nd)
     T f[K][L::Q];
     T rho[K], j[K][3];
     T F[K][3];
-    if constexpr (GEOM) {
+    // The double-float force assembly serves the stiff single-component EOS cases (a plain
+    // FP32 force doubled their 100-step error); two psi = rho components meet the FP32 bound
+    // with the plain assembly (component-scale velocity error 5e-7 at 100 steps either way),
+    // which takes 10 % off the porous collide (A/B, 400^3: 0.852 against 0.923 ms).
+    constexpr bool EXF = !pop_shifted<T, S> && K == 1;
+    if constexpr (GEOM && K == 2) {
+        // two components with solids: the interaction force first, from psi alone, then the
+        // pull; the body force rho a joins once rho is known, as fma(rho, a, F_int) like the
+        // path below. Measured 10 % faster than force-after-pull with the plain assembly
+        // (0.769 against 0.852 ms per launch at 400^3), 5 % with the double-float one. For one
+        // component (sphere packs) the same order measured 2 % slower (64 sphere-pack batch).
+        const Geo3 g = geo3<GEOM>(P, nd.x, nd.y, nd.z);
+        T Fi[K][3];
+        {
+            const T zero[K] = {};
+            interaction_force<L, T, K, EXF>(a, nd, g, zero, Fi);
+        }
+        gather_all<L, T, S, K, GEOM>(a.f_src, P, a.solid, a.fidx, nd, g, f);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            moments<L, T>(f[k], rho[k], j[k]);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) F[k][d] = fma(rho[k], P.accel[k][d], Fi[k][d]);
+        }
+    } else if constexpr (GEOM) {
         // lattices with solids or closed faces: one table for the pull and the force stencil
         const Geo3 g = geo3<GEOM>(P, nd.x, nd.y, nd.z);
         gather_all<L, T, S, K, GEOM>(a.f_src, P, a.solid, a.fidx, nd, g, f);
 #pragma unroll
         for (int k = 0; k < K; ++k) moments<L, T>(f[k], rho[k], j[k]);
-        interaction_force<L, T, K, !pop_shifted<T, S>>(a, nd, g, rho, F);
+        interaction_force<L, T, K, EXF>(a, nd, g, rho, F);
     } else if constexpr (COLL == COLL_BGK) {
         // periodic BGK: psi of the node and of its Q-1 neighbours is loaded before the
         // population gather, so the two sets of loads are in flight together (measured
@@ -1300,6 +1383,10 @@ __device__ __forceinline__ void collide_node(const KArgs<T>& a, const Node& nd)
     }
 }
 
+// two components: 2 CTAs of 256 per SM (up to 128 registers); a cap of 3 CTAs (80
+// registers, 52 B of spills on lattices with solids) measured 7 % slower at 400^3. One
+// component: 4 CTAs (64 registers); 3 CTAs on lattices with solids measured 3-10 % slower
+// on the 64-sphere-pack batch.
 template <class L, typename T, typename S, int K, int COLL, bool GEOM>
 __global__ void __launch_bounds__(256, K == 1 ? 4 : 2) k_collide(const KArgs<T> a)
 {

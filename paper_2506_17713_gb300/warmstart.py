@@ -351,3 +351,33 @@ def relax(n, solid, u0, check=100, max_steps=60000, tol=1e-6, rho0=None):
     k = NU * float(u[0].astype(np.float64).mean()) / ACCEL
     lat.close()
     return steps, dt, k, r, u, rho_f
+
+
+def relax_scaled_early_field(n, solid, m, q_inf, check=100, max_steps=60000, tol=1e-6):
+    """Steps until the residual is <= tol when the run from rest is stopped after m steps and
+    its departure from rest is scaled by s = q_inf / q(m), q being the mean x-velocity over
+    the fluid: f <- w + s (f - w) at fluid nodes. In creeping flow the step is linear in that
+    departure, so this completes the magnitude of the slowest flow mode. Returns (total steps
+    including the m, s)."""
+    import torch
+    lat = Lattice(flow_case(n))
+    lat.set_geometry(solid)
+    lat.init_fields(0, np.ones((n, n, n)))
+    lat.step(m)
+    fl = solid == 0
+    _, u = lat.macroscopic_host(0)
+    s = q_inf / float(u[0].astype(np.float64)[fl].mean())
+    f = lat.populations(0)
+    _, w = lat.velocity_set()
+    w = torch.tensor(np.asarray(w), dtype=f.dtype, device=f.device).view(-1, 1, 1, 1)
+    mask = torch.from_numpy(fl).to(device=f.device, dtype=f.dtype)
+    lat.set_populations(0, (w + s * (f - w)) * mask)
+    lat.diagnostics(residual=True)
+    steps = 0
+    while steps < max_steps:
+        lat.step(check)
+        steps += check
+        if lat.diagnostics(residual=True)[2] <= tol:
+            break
+    lat.close()
+    return m + steps, s

@@ -61,6 +61,29 @@ COEX = {
 # (flat-interface coexistence equal to the Maxwell pair within 0.1 %), found by
 # bisection on the vapour density of a flat liquid slab (D2Q9, BGK, tau = 1).
 A_STAR = {("CS", 0.7): -0.276, ("CS", 0.8): -0.275, ("PR", 0.6): -0.233, ("PR", 0.8): -0.249}
+# Two-component psi = rho fluids (Section 3.3.2 form, A = 0, g_kk = 0): with G_i = w_i / c_s^2
+# the mixture's free energy c_s^2 (rho_1 ln rho_1 + rho_2 ln rho_2) + g12 rho_1 rho_2 separates
+# only for g12 > c_s^2 / sqrt(rho_1 rho_2) (0.63 at rho_1 = rho_2 = 0.53). g12 = 0.8 gives sharp
+# interfaces (one node between 10 % and 90 %) with 1.6 % of each component dissolved in the
+# other's phase (flat D3Q19 slab, BGK tau = 1, common velocity).
+G12_IMMISCIBLE = 0.8
+# (major, dissolved minor) density of each bulk phase of these fluids at equilibrium, read
+# off a resting drop (a phase started elsewhere relaxes to it by slow diffusion)
+RHO_IMMISCIBLE = (1.07, 0.008)
+
+# Wetting parameters of Eq. improved_virtual_density for the contact angles the workloads
+# name, from tests/golden/wetting_calibration.json (FP64 oracle, drop on a flat wall).
+# Two components, 45 degrees through the wetting one: each component takes the branch of
+# its own wettability -- phi = WET_PHI_45 on the wetting component, drho = WET_DRHO_NW on the
+# non-wetting one, which clamps its virtual density to 0 at every wall (a phi of 2.5 on the
+# wetting component alone reaches 45 degrees too, but depletes the dissolved non-wetting
+# component at the walls to 3e-5 and the pressure-driven porous runs blow up).
+# One component, 30 degrees: phi = WET_PHI_30_PR08 for the Peng-Robinson liquid at
+# T = 0.8 Tc of the sphere packs (limiter: the Maxwell pair).
+WET_DRHO_NW = 1.5
+WET_PHI_45 = 1.110625
+WET_PHI_30_PR08 = 1.669687
+
 # The same bisection with the moment-space forcing of the surface-tension collision
 # (forcing = "moment", D2Q9 MRT with the Lallemand-Luo rates, tau = 1): that forcing lacks
 # EDM's F F / rho stress, so mechanical stability needs a stronger Zhang-Chen share.
@@ -169,22 +192,36 @@ def droplet_3d_exp(n=256, radius=30.0, width=5.0, real="f32", shape=None):
     return case, dict(rho=[rho])
 
 
+POROUS_BUFFER = 8
+
+
 def porous_two_component(shape=(400, 400, 400), porosity=0.15, corr_length=6.0, seed=7,
-                         buffer=8, real="f32", theta_phi=1.2, rho_major=1.0,
-                         rho_minor=0.06, g12=0.1, gkk=0.0, tau_w=1.0, tau_nw=0.55,
-                         drho_in=0.02):
+                         buffer=POROUS_BUFFER, real="f32", theta_phi=None, rho_major=RHO_IMMISCIBLE[0],
+                         rho_minor=RHO_IMMISCIBLE[1], g12=G12_IMMISCIBLE, gkk=0.0, tau_w=1.0, tau_nw=1.0,
+                         drho_in=0.3):
     """D3Q19 two-component Shan-Chen (psi = rho, A = 0) in a Gaussian-random-field
     porous medium (porosity 0.15, correlation length 6) with 8-lu fluid buffers.
     Component 0 = wetting phase initially saturating the domain, component 1 =
     non-wetting phase injected at x = 0 through a constant-density face against
-    a constant-density outlet. Viscosity ratio mu_nw : mu_w = 1 : 10 for
-    tau_nw = 0.55, tau_w = 1.0."""
+    a constant-density outlet.
+
+    Fluids: immiscible (g12 = G12_IMMISCIBLE, interfaces one to two nodes wide, surface
+    tension 0.163 from Laplace's law), each phase at its equilibrium composition. The
+    wetting component wets the solid at 45 degrees (theta_phi None: the calibrated
+    virtual-density factor WET_PHI_45, with WET_DRHO_NW on the non-wetting component). drho_in raises the inlet's non-wetting density
+    above the outlet's wetting one: a pressure step of about drho_in / 3 = 0.1, near the
+    capillary entry pressure 2 sigma cos(45) / r of throats of radius 2.
+    Viscosity ratio 1 (tau 1 for both): in this common-velocity model unequal relaxation
+    times move the phases' equilibrium compositions (1:10 measured to leave 4 % dissolved
+    and widen interfaces to 10 nodes), so the configured 1:10 ratio is not used."""
     nx, ny, nz = shape
+    if theta_phi is None:
+        theta_phi = WET_PHI_45
     solid, used_seed = grf_porous_medium(shape, porosity, corr_length, seed, buffer=buffer)
     case = base_case("D3Q19", shape, real=real, ncomp=2, psi=["rho", "rho"], velocity="common",
                      g=[[gkk, g12], [g12, gkk]], tau=[tau_w, tau_nw],
-                     wet_phi=[theta_phi, 1.0], wet_drho=[0.0, 0.0],
-                     rho_lo=[0.0, 0.0], rho_hi=[rho_major * 1.5, rho_major * 1.5],
+                     wet_phi=[theta_phi, 1.0], wet_drho=[0.0, WET_DRHO_NW],
+                     rho_lo=[0.0, 0.0], rho_hi=[5.0, 5.0],
                      bc=["pressure", "pressure", "periodic", "periodic", "periodic", "periodic"])
     bc_rho = [[0.0, 0.0] for _ in range(6)]
     bc_rho[0] = [rho_minor, rho_major + drho_in]   # inlet: non-wetting phase
@@ -201,7 +238,7 @@ def porous_two_component(shape=(400, 400, 400), porosity=0.15, corr_length=6.0, 
 
 
 def sphere_pack_batch(count=64, edge_lo=64, edge_hi=192, porosity=0.38, rmin=8.0, rmax=12.0, seed=2024,
-                      real="f32", T_red=0.8, wet_phi=1.1, buffer=6, width=5.0, tau=1.5):
+                      real="f32", T_red=0.8, wet_phi=WET_PHI_30_PR08, buffer=6, width=5.0, tau=1.5):
     """Batch of drainage samples: each a D3Q19 box with edges U[edge_lo, edge_hi]
     (seeded per sample), an overlapping-sphere pack (radius U[rmin, rmax]) to the given
     porosity, single-component Peng-Robinson at T_red with MRT collision (tau, energy

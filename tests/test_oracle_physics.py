@@ -3,13 +3,16 @@
 Poiseuille flow (exact for BGK halfway bounce-back at tau = 1/2 + sqrt(3/16)),
 cocurrent two-layer channel flow against its layered Stokes solution (Section 3.4.2),
 flat-interface coexistence against the Maxwell construction (Section 3.1, D2Q9 and
-D3Q19), Laplace's law (Section 3.2; 2-D, and 3-D with Delta p = 2 sigma / R), neutral wetting (phi = 1, drho = 0 gives 90
-degrees, Section 3.3.2) and the monotone effect of phi / drho (Section 2.4).
+D3Q19), Laplace's law (Section 3.2; 2-D, and 3-D with Delta p = 2 sigma / R), wetting
+(Section 2.4): the contact-angle measurement on a mirror wall, neutral phi = 1 near 90
+degrees (Section 3.3.2), the monotone effect of phi / drho, and the calibrated phi of the
+workloads reproducing their set angles.
 """
 import numpy as np
 import pytest
 
 import oracle
+import wetting
 from synth import cases, droplet_field
 
 
@@ -170,41 +173,57 @@ def test_flat_interface_coexistence_d3q19(eos, Tr):
     assert np.abs(u).max() < 1e-2
 
 
-def _sessile(phi, drho, steps=6000):
-    nx, ny, R = 80, 40, 14.0
-    A = cases.A_STAR[("CS", 0.7)]
-    case = cases.base_case("D2Q9", (nx, ny, 1), A=[A, A], wet_phi=[phi, phi], wet_drho=[drho, drho],
-                           bc=["periodic", "periodic", "wall", "wall", "periodic", "periodic"])
-    case = cases.with_eos(case, "CS", 0.7)
-    case["eos_a"] = [0.5, 0.5]
-    rg, rl = cases.COEX[("CS", 0.7)]
-    case["rho_lo"] = [rg, rg]
-    case["rho_hi"] = [rl, rl]
-    solid = np.zeros((1, ny, nx), dtype=np.uint8)
-    solid[0, 0, :] = 1
-    rho = droplet_field((nx, ny, 1), [(nx / 2, 0.5)], [R], rl, rg, 5.0, periodic=False)
+def _sessile(phi, drho, steps=3000):
+    # D2Q9 CS drop on the solid row y = 0 (tests/wetting.py), angle by the circle fit
+    case, rhos, solid, ind = wetting.sessile_case("cs_d2q9", phi)
+    case["wet_drho"] = [drho, drho]
     s = oracle.OracleSim(case)
     s.set_geometry(solid)
-    s.init_fields(0, rho)
+    s.init_fields(0, rhos[0])
     s.step(steps)
-    r, _ = s.macroscopic(0)
-    mid = 0.5 * (rl + rg)
-    wet = r[0] > mid
-    L = wet[1].sum()                       # base width on the first fluid layer
-    h = wet[:, nx // 2].sum()              # height along the axis (fluid layers)
-    return np.degrees(2 * np.arctan2(2 * h, L))
+    a, mid = ind([s.macroscopic(0)[0][0]])
+    return wetting.circle_angle(a, mid)
 
 
-def test_neutral_wetting_gives_ninety_degrees():
-    assert abs(_sessile(1.0, 0.0) - 90.0) < 6.0
+def test_contact_angle_measurement_on_a_mirror_wall():
+    # the measurement itself: with no solid row, a WALL face's clamped stencil mirrors the
+    # fluid about the plane half a link outside the first row, so the drop is exactly half
+    # of a free drop and makes 90 degrees; the circle fit finds 89.4
+    case, rhos, solid, ind = wetting.sessile_case("cs_d2q9", 1.0)
+    nx, ny = case["shape"][0], case["shape"][1]
+    rg, rl = cases.COEX[("CS", 0.7)]
+    s = oracle.OracleSim(case)
+    s.init_fields(0, droplet_field((nx, ny, 1), [(nx / 2, -0.5)], [20.0], rl, rg, 5.0, periodic=False))
+    s.step(3000)
+    theta = wetting.circle_angle(s.macroscopic(0)[0][0], 0.5 * (rl + rg), wall_y=-0.5)
+    assert abs(theta - 90.0) < 1.0
+
+
+def test_neutral_wetting_close_to_ninety_degrees():
+    # phi = 1, drho = 0 is the neutral setting (Section 3.3.2: 90 degrees). The improved
+    # virtual density averages the first fluid layer with the lattice weights, which smooths
+    # the density along the wall by rho''/6 at the contact line: 86.7 degrees here (89.4 on
+    # the mirror wall above), the same in D3Q19 (86.5 for the Peng-Robinson drop)
+    assert abs(_sessile(1.0, 0.0) - 90.0) < 4.0
 
 
 def test_wetting_parameters_move_contact_angle():
-    neutral = _sessile(1.0, 0.0, steps=4000)
-    hydrophilic = _sessile(1.15, 0.0, steps=4000)
-    hydrophobic = _sessile(1.0, 0.04, steps=4000)
+    neutral = _sessile(1.0, 0.0)
+    hydrophilic = _sessile(1.15, 0.0)
+    hydrophobic = _sessile(1.0, 0.04)
     assert hydrophilic < neutral - 10
     assert hydrophobic > neutral + 10
+
+
+@pytest.mark.parametrize("model", ["pr08", "two_component"])
+def test_calibrated_wetting_reproduces_the_set_angle(model):
+    # the phi of tests/golden/wetting_calibration.json (written by its script from the
+    # oracle) gives the angle the workload names: 30 degrees for the sphere-pack fluid,
+    # 45 degrees for the porous drainage fluids, within 1 degree
+    cal = wetting.calibration()[model]
+    theta = wetting.oracle_angle(model, cal["phi"], cal["steps"], shape=tuple(cal["shape"]), radius=cal["radius"],
+                                 theta0=cal["theta0"])
+    assert abs(theta - cal["theta_set"]) < 1.0
 
 
 def test_cocurrent_two_layer_channel_against_closed_form():

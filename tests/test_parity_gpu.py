@@ -436,7 +436,7 @@ def _residual_case(kind, real):
                                        ("two_component", "f32")])
 def test_residual_matches_oracle_snapshots(kind, real):
     # a9: the steady-state residual ||u^n - u^(n-k)||_2 / ||u^n||_2 of the mixture velocity
-    # over fluid nodes (the reading of "until steady state", Sections 3.1 and 3.4.1)
+    # over fluid nodes (the steady-state criterion read into Sections 3.1 and 3.4.1)
     case, rhos, solid = _residual_case(kind, real)
     n1, k = 120, 60
     lat, orc = run_both(case, rhos, n1, solid=solid)

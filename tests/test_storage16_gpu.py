@@ -17,12 +17,18 @@ Summed over directions (positive populations, sum_i w_i = 1) this gives
   |drho| <= 3 u_s (rho_max + rho_ref) + (FP32 compute, < 1e-5 rho_max),
 checked here as a relative L-inf bound on the density.
 
-The velocity error is reported, not bounded. In a resting droplet the velocity is the
-spurious current, orders of magnitude below the population rounding, so its relative
-error is large: 16-bit storage is inaccurate at high density ratios. On a weakly
-non-uniform lattice (density 0.8 to 1.2, reference density 1) the stored deviations
-are small, and 100 steps stay within the linear accumulation bound
-  100 u_s max|f - w rho_ref| / rho_min per component of the velocity scale.
+In a resting droplet the velocity is the spurious current, orders of magnitude below
+the population rounding, so its relative error is large (reported, not bounded): 16-bit
+storage is inaccurate at high density ratios. On a weakly non-uniform lattice (density
+0.8 to 1.2, reference density 1) the stored deviations are small: |f_i - w_i| <= 0.3 w_i
+there (density deviation 0.2 plus the non-equilibrium part), so one rounding of every
+population moves j_x by at most u_s 0.3 sum_i w_i |e_ix| = 0.1 u_s, and 100 steps of
+linear accumulation keep the velocity within 100 x 0.1 u_s / rho_min of the oracle.
+
+What the paper's physics tolerance asks of 16-bit storage is checked on an observable:
+a Peng-Robinson droplet at T = 0.6 Tc (density ratio 853) relaxed for 2000 steps keeps
+its liquid and vapour densities and its Laplace pressure jump within 1 % of the FP32
+path with FP16 storage, and within 8 % (the ratio of the unit roundoffs) with BF16.
 """
 import numpy as np
 import pytest
@@ -111,8 +117,51 @@ def test_weakly_nonuniform_100_steps(real):
     eu = max(np.abs(ug[d].astype(np.float64) - uo[d]).max() for d in range(3)) / uscale
     # |f_i - w_i| <= w_i * 0.2 + |f_neq| <= 0.1 here; linear accumulation over 100 steps
     bound_r = 100 * US[real] * 0.1 / 0.8
-    print("%s weakly non-uniform 100 steps: rho %.3e (bound %.3e), u/u_scale %.3e" % (real, er, bound_r, eu))
+    eu_abs = eu * uscale
+    bound_u = 100 * 0.1 * US[real] / 0.8
+    print("%s weakly non-uniform 100 steps: rho %.3e (bound %.3e), u/u_scale %.3e, |du| %.3e (bound %.3e)"
+          % (real, er, bound_r, eu, eu_abs, bound_u))
     assert er <= bound_r
+    assert eu_abs <= bound_u
+
+
+@pytest.mark.parametrize("real", ["f16s", "bf16s"])
+def test_droplet_observables_within_one_percent_of_fp32(real):
+    # the physics observables of the 256^3 droplet workload (coexistence densities and
+    # the Laplace jump of Section 3.2) after the interface has relaxed, 16-bit storage
+    # against FP32 storage on the same GPU path; FP64 oracle for the record
+    from paper_2506_17713_gb300 import Lattice
+    shape = (48, 48, 48)
+    obs = {}
+    for r in ("f32", real, "oracle"):
+        case, init = cases.droplets_3d_pr(shape=shape, count=1, rmin=12.0, rmax=12.0, seed=5)
+        case["real"] = "f64" if r == "oracle" else r
+        case["rho_ref"] = [cases.COEX[("PR", 0.6)][0]] * 2
+        if r == "oracle":
+            if real != "f16s":
+                continue
+            sim = oracle.OracleSim(case)
+            sim.init_fields(0, init["rho"][0])
+            sim.step(2000)
+            rho = sim.macroscopic(0)[0]
+        else:
+            lat = Lattice(case)
+            lat.init_fields(0, init["rho"][0])
+            lat.step(2000)
+            rho = lat.macroscopic_host(0)[0].astype(np.float64)
+        c = np.unravel_index(np.argmax(rho), rho.shape)
+        core = rho[tuple(slice(max(i - 2, 0), i + 3) for i in c)].mean()
+        far = tuple((i + 24) % 48 for i in c)
+        vap = rho[tuple(slice(i - 2, i + 3) for i in far)].mean()
+        dp = oracle.bulk_pressure(case, 0, core) - oracle.bulk_pressure(case, 0, vap)
+        obs[r] = np.array([core, vap, dp])
+    tol = 0.01 * US[real] / US["f16s"]
+    rel = np.abs(obs[real] / obs["f32"] - 1)
+    msg = "%s vs FP32 after 2000 steps: rho_l %.2e, rho_g %.2e, Delta p %.2e (tol %.2g)" % ((real,) + tuple(rel) + (tol,))
+    if "oracle" in obs:
+        msg += "; FP32 vs FP64 oracle %s" % np.array2string(np.abs(obs["f32"] / obs["oracle"] - 1), precision=2)
+    print(msg)
+    assert np.all(rel <= tol)
 
 
 @pytest.mark.parametrize("real", ["f16s", "bf16s"])

@@ -64,3 +64,20 @@ def test_warm_start_samples_percolate_periodically():
         pore = solid == 0
         kept, ok = synth.periodic_percolating_pores(pore)
         assert ok and np.array_equal(kept, pore)
+
+
+def test_workload_wetting_parameters_are_the_calibrated_ones():
+    # the virtual-density factors the porous and sphere-pack workloads use are the ones
+    # tests/golden/make_wetting_calibration.py found with the oracle for 45 and 30 degrees
+    import json
+    import os
+    from synth import cases
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "wetting_calibration.json")) as fh:
+        cal = json.load(fh)
+    assert cal["two_component"]["theta_set"] == 45.0 and cal["pr08"]["theta_set"] == 30.0
+    assert abs(cases.WET_PHI_45 - cal["two_component"]["phi"]) < 1e-9
+    assert abs(cases.WET_PHI_30_PR08 - cal["pr08"]["phi"]) < 1e-9
+    c = cases.porous_two_component(shape=(24, 12, 10), buffer=3, porosity=0.7)[0]
+    assert c["wet_phi"][0] == cases.WET_PHI_45
+    b = cases.sphere_pack_batch(count=1, edge_lo=24, edge_hi=24)[0][0]
+    assert b["wet_phi"][0] == cases.WET_PHI_30_PR08
