@@ -585,6 +585,26 @@ LBM_HD void gather_all(const void* f_all, const Params<T>& P, const uint8_t* __r
 {
     const long long N = P.N;
     const S* fs = static_cast<const S*>(f_all) + (long long)k0 * L::Q * N;
+    if constexpr (GEOM && K == 1) {
+        if (fidx && g.fl == 0u) {
+            // a node on no closed face (almost every node): no pull crosses a face, so a
+            // direction is pulled from its source's slot, or bounces back where the slot map
+            // marks a solid -- the face logic below reduces to this. One component only: the
+            // one-component collide drops its 28 B of spills with it (sphere packs, 17.9 ->
+            // 18.5 GLUPS sequential), while the two-component kernels spill more and slow
+            // down (porous 400^3: 81.6 -> 71.9 GLUPS)
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) {
+                const int src = g.xo[L::ex(i) + 1] + g.yo[L::ey(i) + 1] + g.zo[L::ez(i) + 1];
+                const int js = i == 0 ? (int)nd.slot : fidx[src];
+                const long long m = js < 0 ? (long long)L::opp(i) * N + nd.slot : (long long)i * N + js;
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+                    f[k][i] = load_pop<L, T, S>(fs, (long long)k * L::Q * N + m, i, P.rho_ref[k0 + k]);
+            }
+            return;
+        }
+    }
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
         const int src = g.xo[L::ex(i) + 1] + g.yo[L::ey(i) + 1] + g.zo[L::ez(i) + 1];
@@ -1285,17 +1305,17 @@ __device__ __forceinline__ void collide_node(const KArgs<T>& a, const Node& nd)
     T f[K][L::Q];
     T rho[K], j[K][3];
     T F[K][3];
-    // The double-float force assembly serves the stiff single-component EOS cases (a plain
-    // FP32 force doubled their 100-step error); two psi = rho components meet the FP32 bound
-    // with the plain assembly (component-scale velocity error 5e-7 at 100 steps either way),
-    // which takes 10 % off the porous collide (A/B, 400^3: 0.852 against 0.923 ms).
-    constexpr bool EXF = !pop_shifted<T, S> && K == 1;
+    // The force assembly is double-float in FP32 and FP64: at a resting interface the
+    // interaction force exceeds a driving body force by orders of magnitude (1e5 in the
+    // two-layer channel), and the layer fluxes of that channel after 150 000 steps moved by
+    // 1.6e-3 with a plain FP32 assembly (10 % faster on the porous workload, not kept).
+    constexpr bool EXF = !pop_shifted<T, S>;
     if constexpr (GEOM && K == 2) {
         // two components with solids: the interaction force first, from psi alone, then the
         // pull; the body force rho a joins once rho is known, as fma(rho, a, F_int) like the
-        // path below. Measured 10 % faster than force-after-pull with the plain assembly
-        // (0.769 against 0.852 ms per launch at 400^3), 5 % with the double-float one. For one
-        // component (sphere packs) the same order measured 2 % slower (64 sphere-pack batch).
+        // path below. Measured 5 % faster than force-after-pull at 400^3 (0.877 against
+        // 0.923 ms per launch, general double-float assembly). For one component (sphere
+        // packs) the same order measured 2 % slower (64 sphere-pack batch).
         const Geo3 g = geo3<GEOM>(P, nd.x, nd.y, nd.z);
         T Fi[K][3];
         {

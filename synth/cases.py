@@ -55,6 +55,7 @@ COEX = {
     ("PR", 0.8): (0.197079, 7.20405),
     ("CS", 0.8): (0.0217232, 0.307196),
     ("VdW", 0.8): (0.838834, 6.76447),
+    ("VdW", 0.7): (0.448078, 7.49155),        # a = 9/49, b = 2/21
 }
 
 # Zhang-Chen / Shan-Chen mixing weight A_kk that satisfies mechanical stability
@@ -87,7 +88,11 @@ WET_PHI_30_PR08 = 1.669687
 # The same bisection with the moment-space forcing of the surface-tension collision
 # (forcing = "moment", D2Q9 MRT with the Lallemand-Luo rates, tau = 1): that forcing lacks
 # EDM's F F / rho stress, so mechanical stability needs a stronger Zhang-Chen share.
-A_STAR_MOMENT = {("CS", 0.7): -0.886}
+A_STAR_MOMENT = {("CS", 0.7): -0.886, ("VdW", 0.7): -0.494}
+# van der Waals at T = 0.7 Tc (a = 9/49, b = 2/21: the capillary-rise fluid of Section 3.4.1):
+# c_s^2 rho - p < 0 inside the loop for alpha = 1, so the pressure scaling alpha = 0.5
+# keeps psi real (the Maxwell pair is that of p itself); its A* above is for that alpha
+VDW07_ALPHA = 0.5
 
 # Peng-Robinson at T = 0.6 Tc (density ratio 853): the liquid sits close to the
 # repulsive pole 1/b, so the EOS is stiff and droplets blow up with alpha = 1.

@@ -5,10 +5,13 @@ names, found with the FP64 oracle alone.
   sphere-pack drainage fluid (Peng-Robinson, T = 0.8 Tc):  30 degrees
   porous drainage fluids (two components, psi = rho):     45 degrees (through the wetting one;
                                                           phi on it, drho = WET_DRHO_NW on the other)
+  capillary-rise fluid (van der Waals, T = 0.7 Tc,
+    kappa = 0.5, Section 3.4.1):                          19 degrees
 
 The angle is measured on a drop resting on a flat wall (tests/wetting.py). theta(phi)
 decreases monotonically; the script brackets the target and bisects to 0.25 degrees.
-Run from the repository root: python tests/golden/make_wetting_calibration.py
+Run from the repository root: python tests/golden/make_wetting_calibration.py [model ...]
+(no model: all; the others keep their stored entries).
 """
 import json
 import os
@@ -24,6 +27,7 @@ import wetting  # noqa: E402
 TARGETS = {
     "pr08": dict(theta=30.0, shape=(200, 60, 2), radius=22.0, steps=6000, lo=1.0, hi=2.5),
     "two_component": dict(theta=45.0, shape=(120, 60, 2), radius=22.0, steps=6000, lo=0.95, hi=1.4),
+    "vdw07_kappa": dict(theta=19.0, shape=(320, 60, 1), radius=30.0, steps=8000, lo=1.4, hi=2.5),
 }
 
 
@@ -60,14 +64,20 @@ def calibrate(model, t):
 
 
 def main():
+    path = os.path.join(HERE, "wetting_calibration.json")
     out = {}
+    if len(sys.argv) > 1 and os.path.exists(path):
+        with open(path) as fh:
+            out = json.load(fh)
     for model, t in TARGETS.items():
+        if len(sys.argv) > 1 and model not in sys.argv[1:]:
+            continue
         phi, th = calibrate(model, t)
         out[model] = dict(theta_set=t["theta"], phi=round(phi, 6), theta_oracle=round(th, 4),
                           shape=list(t["shape"]), radius=t["radius"], steps=t["steps"], theta0=t["theta"])
     out["_source"] = ("FP64 oracle, sessile drop on a flat wall, circle fit of the half-way iso-line "
                       "(tests/wetting.py); written by tests/golden/make_wetting_calibration.py")
-    with open(os.path.join(HERE, "wetting_calibration.json"), "w") as fh:
+    with open(path, "w") as fh:
         json.dump(out, fh, indent=1)
     print(json.dumps(out, indent=1))
 

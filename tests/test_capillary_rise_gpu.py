@@ -1,21 +1,19 @@
-"""Capillary rise (horizontal imbibition) in a slit, Section 3.4.1, on the CUDA
-path: D2Q9 MRT, surface-tension adjustment kappa = 0.5, liquid reservoir at the
-channel entrance, periodic box.
-
-The paper uses van der Waals at T = 0.7 T_c. Van der Waals needs alpha < 1 to keep
-c_s^2 rho - p positive inside the loop, and its mixing weight is not calibrated
-here, so the test uses the calibrated Carnahan-Starling case at T = 0.7 T_c; the
-slit is 20 wide (paper: 28) and 200 long (paper: 300).
+"""Capillary rise (horizontal imbibition) in a channel, Section 3.4.1, on the CUDA path,
+in the paper's set-up: D2Q9 MRT with the surface-tension adjustment kappa = 0.5 (and the
+moment-space forcing of Eq. mrt_surface), van der Waals fluid (a = 9/49, b = 2/21, R = 1,
+T = 0.7 Tc; pressure scaling alpha = 0.5, which keeps psi real), a 600 x 100 periodic box
+with a channel of length 300 and width 28 cut through a solid block at 150 < x < 450, liquid
+at x < 150, static contact angle 19 degrees (the calibrated virtual density of
+tests/golden/wetting_calibration.json).
 
 Checked:
-- wetting walls (phi > 1) draw the liquid in monotonically, non-wetting walls
-  (phi = 1, drho > 0) do not;
+- the wetting channel draws the liquid in monotonically, a non-wetting one (phi = 1,
+  drho > 0) does not;
 - once viscous resistance dominates, l^2 grows linearly in t (Lucas-Washburn);
 - the meniscus position against the RK4 solution of the imbibition equation
-  (oracle/washburn.py), with sigma from a Laplace fit and the dynamic contact
-  angle from the meniscus depth h_m (theta_d = acos(4 h_m H / (H^2 + 4 h_m^2)),
-  both measured on the same model). The ratio is stated and bounded; the
-  simulation runs 20-25 % ahead of the equation here.
+  (oracle/washburn.py), with sigma from a Laplace fit of the same model and the dynamic
+  contact angle from the meniscus depth h_m (theta_d = acos(4 h_m H / (H^2 + 4 h_m^2))).
+  The paper reports close agreement without a number; the ratio is printed and bounded.
 """
 import math
 
@@ -23,14 +21,15 @@ import numpy as np
 import pytest
 
 import oracle
+import wetting
 from oracle import washburn
-from synth import cases
+from synth import cases, droplet_field
 
 pytestmark = pytest.mark.gpu
 
-RG, RL = cases.COEX[("CS", 0.7)]
+RG, RL = cases.COEX[("VdW", 0.7)]
 KAPPA = 0.5
-NX, NY, X0, X1, H, TW = 400, 60, 100, 300, 20, 4
+NX, NY, X0, X1, H = 600, 100, 150, 450, 28
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -43,43 +42,54 @@ def _gpu():
 
 
 def _case(shape, phi=1.0, drho=0.0):
-    A = cases.A_STAR[("CS", 0.7)]
-    c = cases.with_eos(cases.base_case("D2Q9", shape, collision="MRT", A=[A, A], kappa=[KAPPA, KAPPA],
-                                       wet_phi=[phi, phi], wet_drho=[drho, drho]), "CS", 0.7)
-    c["eos_a"] = [0.5, 0.5]
+    A = cases.A_STAR_MOMENT[("VdW", 0.7)]
+    c = cases.with_eos(cases.base_case("D2Q9", shape, collision="MRT", A=[A, A], alpha=[cases.VDW07_ALPHA] * 2,
+                                       kappa=[KAPPA, KAPPA], forcing="moment",
+                                       wet_phi=[phi, phi], wet_drho=[drho, drho]), "VdW", 0.7)
     c["rho_lo"] = [RG, RG]
     c["rho_hi"] = [RL, RL]
     return c
 
 
 def _sigma():
+    # Laplace's law on drops of the same model resting on a flat wall (tests/wetting.py): the
+    # same area at three wetting strengths gives three cap radii R (circle fit); the jump
+    # between the liquid under the cap's top and the far vapour is sigma / R (2-D). Free
+    # droplets of this fluid are not used: their w = 5 tanh start reaches |u| = 0.2 within
+    # five steps and several radii blow up (oracle and GPU alike).
     from paper_2506_17713_gb300 import Lattice
     pts = []
-    for R in (12, 16, 20):
-        case, init = cases.droplet_2d_cs(n=96, radius=R)
-        case = dict(case, collision="MRT", kappa=[KAPPA, KAPPA])
+    for phi in (1.0, 1.2, 1.4):
+        case, rhos, solid, ind = wetting.sessile_case("vdw07_kappa", phi, real="f32", theta0=19.0)
         lat = Lattice(case)
-        lat.init_fields(0, init["rho"][0])
+        lat.set_geometry(solid)
+        lat.init_fields(0, rhos[0])
         lat.step(8000)
-        r, _ = lat.macroscopic_host(0)
-        r = r.astype(float)
-        rin, rout = r[0, 45:51, 45:51].mean(), r[0, :4, :4].mean()
+        r = lat.macroscopic_host(0)[0][0].astype(float)
+        lat.close()
+        theta, R, xc, yc = wetting.circle_fit(r, 0.5 * (RL + RG))
+        x = int(round(xc))
+        rin = r[2:5, x - 2:x + 3].mean()
+        rout = r[-6:-2, :10].mean()
         dp = oracle.bulk_pressure(case, 0, rin) - oracle.bulk_pressure(case, 0, rout)
-        pts.append((1.0 / math.sqrt((r > 0.5 * (rin + rout)).sum() / math.pi), dp))
+        pts.append((1.0 / R, dp))
     x = np.array(pts)
     (sig, _), *_ = np.linalg.lstsq(np.vstack([x[:, 0], np.ones(3)]).T, x[:, 1], rcond=None)
     return sig
 
 
-def _imbibition(phi, drho=0.0, steps=28000, every=500):
-    """meniscus position l(t) on the channel axis and next to the wall"""
+def _imbibition(phi, drho=0.0, steps=80000, every=1000):
+    """meniscus position l(t) on the channel axis and next to the wall: the channel is cut
+    through a solid block that fills the box height outside it for X0 <= x < X1"""
     from paper_2506_17713_gb300 import Lattice
     y0 = (NY - H) // 2
     solid = np.zeros((1, NY, NX), np.uint8)
-    solid[0, y0 - TW:y0, X0:X1] = 1
-    solid[0, y0 + H:y0 + H + TW, X0:X1] = 1
+    solid[0, :y0, X0:X1] = 1
+    solid[0, y0 + H:, X0:X1] = 1
     X = np.arange(NX)[None, None, :] * np.ones((1, NY, 1))
-    rho = 0.5 * (RL + RG) - 0.5 * (RL - RG) * np.tanh(2 * (X - X0) / 4.0)
+    d = np.abs(X - X0 / 2)
+    d = np.minimum(d, NX - d)                    # periodic distance to the slab centre
+    rho = 0.5 * (RL + RG) - 0.5 * (RL - RG) * np.tanh(2 * (d - X0 / 2) / 5.0)
     lat = Lattice(_case((NX, NY, 1), phi, drho))
     lat.set_geometry(solid)
     lat.init_fields(0, rho)
@@ -96,19 +106,20 @@ def _imbibition(phi, drho=0.0, steps=28000, every=500):
     t, lc, lw = [], [], []
     for b in range(steps // every):
         lat.step(every)
-        r, _ = lat.macroscopic_host(0)
-        r = r[0].astype(float)
+        r = lat.macroscopic_host(0)[0][0].astype(float)
         t.append((b + 1) * every)
         lc.append(front(r, y0 + H // 2))
         lw.append(front(r, y0))
+    lat.close()
     return np.array(t, float), np.array(lc), np.array(lw)
 
 
-def test_wetting_slit_imbibes_and_follows_the_imbibition_equation():
-    t, lc, lw = _imbibition(1.15)
+def test_wetting_channel_imbibes_and_follows_the_imbibition_equation():
+    phi = wetting.calibration()["vdw07_kappa"]["phi"]
+    t, lc, lw = _imbibition(phi)
     inside = lc < 0.9 * (X1 - X0)
     t, lc, lw = t[inside], lc[inside], lw[inside]
-    assert len(t) > 20 and lc[-1] > 0.3 * (X1 - X0)
+    assert len(t) > 10 and lc[-1] > 0.3 * (X1 - X0)
     assert np.all(np.diff(lc) > 0)                                  # advances monotonically
     # viscous regime: l^2 linear in t over the second half
     h = len(t) // 2
@@ -123,12 +134,12 @@ def test_wetting_slit_imbibes_and_follows_the_imbibition_equation():
     nu = (1.0 - 0.5) / 3.0
     ode = washburn.meniscus(list(t), sig, theta, H, X1 - X0, RL, RG, RL * nu, RG * nu, dt=0.5)
     ratio = lc[-1] / ode[-1]
-    print("sigma %.5f, theta_d %.1f deg, l_LBM %.1f, l_ODE %.1f, ratio %.3f"
-          % (sig, math.degrees(theta), lc[-1], ode[-1], ratio))
-    assert 0.8 < ratio < 1.4
+    print("sigma %.5f, theta_d %.1f deg, samples %d, l_LBM %.1f, l_ODE %.1f, ratio %.3f"
+          % (sig, math.degrees(theta), len(t), lc[-1], ode[-1], ratio))
+    assert 0.8 < ratio < 1.25
 
 
-def test_non_wetting_slit_stays_empty():
+def test_non_wetting_channel_stays_empty():
     # phi = 1, drho > 0: contact angle above 90 degrees (Eq. improved_virtual_density)
-    t, lc, _ = _imbibition(1.0, drho=0.05, steps=8000)
+    t, lc, _ = _imbibition(1.0, drho=1.0, steps=10000)
     assert lc.max() < 6.0

@@ -22,7 +22,7 @@ def _gpu():
     build()
 
 
-@pytest.mark.parametrize("model", ["pr08", "two_component"])
+@pytest.mark.parametrize("model", ["pr08", "two_component", "vdw07_kappa"])
 def test_contact_angle_matches_oracle_within_one_percent(model):
     from paper_2506_17713_gb300 import Lattice
     cal = wetting.calibration()[model]

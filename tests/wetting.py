@@ -28,6 +28,12 @@ def calibration():
 
 def circle_angle(ind, mid, skip=3.0, wall_y=WALL_Y):
     """Contact angle (degrees) of the drop where ind > mid, ind [ny, nx], wall at y = wall_y."""
+    return circle_fit(ind, mid, skip, wall_y)[0]
+
+
+def circle_fit(ind, mid, skip=3.0, wall_y=WALL_Y):
+    """(contact angle in degrees, radius, centre x, centre y) of the circle fitted to the
+    half-way iso-line of the drop where ind > mid, ind [ny, nx], wall at y = wall_y."""
     ny, nx = ind.shape
     pts = []
     a = ind - mid
@@ -47,7 +53,7 @@ def circle_angle(ind, mid, skip=3.0, wall_y=WALL_Y):
     (D, E, F), *_ = np.linalg.lstsq(A, rhs, rcond=None)
     xc, yc = -D / 2, -E / 2
     R = np.sqrt(xc * xc + yc * yc - F)
-    return float(np.degrees(np.arccos(np.clip((wall_y - yc) / R, -1.0, 1.0))))
+    return float(np.degrees(np.arccos(np.clip((wall_y - yc) / R, -1.0, 1.0)))), float(R), float(xc), float(yc)
 
 
 def _cap_centre(radius, theta0):
@@ -79,6 +85,23 @@ def sessile_case(model, phi, shape=None, radius=None, real="f64", theta0=90.0):
         case = cases.with_eos(case, "CS", 0.7)
         case["eos_a"] = [0.5, 0.5]
         rg, rl = cases.COEX[("CS", 0.7)]
+        case["rho_lo"], case["rho_hi"] = [rg, rg], [rl, rl]
+        yc, R0 = _cap_centre(R, theta0)
+        rhos = [droplet_field((nx, ny, nz), [(nx / 2, yc)], [R0], rl, rg, 5.0, periodic=False)]
+        mid = 0.5 * (rl + rg)
+        ind = lambda r: (r[0], mid)
+    elif model == "vdw07_kappa":
+        # the capillary-rise fluid: D2Q9 van der Waals at T = 0.7 Tc (alpha = 0.5), MRT with the
+        # surface-tension adjustment kappa = 0.5 and the moment-space forcing, tau = 1
+        nx, ny, nz = shape or (320, 60, 1)
+        R = radius or 30.0
+        A = cases.A_STAR_MOMENT[("VdW", 0.7)]
+        case = cases.with_eos(cases.base_case("D2Q9", (nx, ny, nz), collision="MRT", A=[A, A], real=real,
+                                              alpha=[cases.VDW07_ALPHA] * 2, kappa=[0.5, 0.5], forcing="moment",
+                                              wet_phi=[phi, phi],
+                                              bc=["periodic", "periodic", "wall", "wall", "periodic", "periodic"]),
+                              "VdW", 0.7)
+        rg, rl = cases.COEX[("VdW", 0.7)]
         case["rho_lo"], case["rho_hi"] = [rg, rg], [rl, rl]
         yc, R0 = _cap_centre(R, theta0)
         rhos = [droplet_field((nx, ny, nz), [(nx / 2, yc)], [R0], rl, rg, 5.0, periodic=False)]
