@@ -330,6 +330,19 @@ LBM_HD void store_pop(S* __restrict__ p, long long m, int i, T v, T rho_ref)
     else p[m] = v;
 }
 
+// The stored value itself: with 16-bit storage the deviation d_i = f_i - w_i rho_ref.
+// The density passes need f only through rho = sum_i d_i + rho_ref (the weights sum to
+// 1), which saves the shift of every load. The collide pass keeps the shifted loads:
+// on the 256^3 PR workload a collide on the deviations measured 3 % slower (0.4366
+// against 0.4234 ms per launch), the density pass on them 4.6 % faster (0.1730 against
+// 0.1813 ms).
+template <typename T, typename S>
+LBM_HD T load_raw(const S* __restrict__ p, long long m)
+{
+    if constexpr (pop_shifted<T, S>) return pop_to_float(p[m]);
+    else return p[m];
+}
+
 // ---------------------------------------------------------------------------
 // Node addressing
 // ---------------------------------------------------------------------------
@@ -440,8 +453,11 @@ LBM_HD int pull_source(const Params<T>& P, const uint8_t* __restrict__ solid, in
 // sign nin): unknown populations have nin * e_x > 0.
 //   rho u_n = rho_b - (sum_{e_x = 0} f + 2 sum_{nin e_x < 0} f)
 //   f_i = f_opp(i) + 6 w_i rho u_n - (e_iy N_y + e_iz N_z) / 2,  N_t = sum_{e_x = 0} f e_t
+// rref != 0: f holds the deviations f_i - w_i rref (16-bit storage); the two face sums
+// then take rref times their weight sums, the rest of the closure is unchanged (opposite
+// directions share their weight, and the tangential sums of w e vanish)
 template <class L, typename T>
-LBM_HD void zou_he(T (&f)[L::Q], int nin, T rho_b)
+LBM_HD void zou_he(T (&f)[L::Q], int nin, T rho_b, T rref = T(0))
 {
     T s0 = T(0), sneg = T(0), Ny = T(0), Nz = T(0);
 #pragma unroll
@@ -454,6 +470,17 @@ LBM_HD void zou_he(T (&f)[L::Q], int nin, T rho_b)
         } else if (en < 0) {
             sneg += f[i];
         }
+    }
+    if (rref != T(0)) {
+        double w0 = 0.0, wn = 0.0;
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const int en = L::ex(i) * nin;
+            if (en == 0) w0 += L::w(i);
+            else if (en < 0) wn += L::w(i);
+        }
+        s0 = fma(T(w0), rref, s0);
+        sneg = fma(T(wn), rref, sneg);
     }
     const T run = rho_b - (s0 + T(2) * sneg);
 #pragma unroll
@@ -578,13 +605,20 @@ LBM_HD int stencil_index(const Geo3& g, int ex, int ey, int ez)
 // (completed by Zou-He) -- is taken once and applied to every component.
 // With fidx (lattices with solids: fluid-only population storage) a source node m
 // holds its populations at slot fidx[m], and fidx[m] < 0 marks a solid.
-template <class L, typename T, typename S, int K, bool GEOM>
+// DEV (16-bit storage only): f receives the stored deviations (load_raw) instead of the
+// populations
+template <class L, typename T, typename S, int K, bool GEOM, bool DEV = false>
 LBM_HD void gather_all(const void* f_all, const Params<T>& P, const uint8_t* __restrict__ solid,
                        const int* __restrict__ fidx, const Node& nd, const Geo3& g, T (&f)[K][L::Q],
                        int k0 = 0)
 {
+    constexpr bool RAW = DEV && pop_shifted<T, S>;
     const long long N = P.N;
     const S* fs = static_cast<const S*>(f_all) + (long long)k0 * L::Q * N;
+    auto ld = [&](long long m, int i, int k) -> T {
+        if constexpr (RAW) return load_raw<T, S>(fs, m);
+        else return load_pop<L, T, S>(fs, m, i, P.rho_ref[k0 + k]);
+    };
     if constexpr (GEOM && K == 1) {
         if (fidx && g.fl == 0u) {
             // a node on no closed face (almost every node): no pull crosses a face, so a
@@ -600,7 +634,7 @@ LBM_HD void gather_all(const void* f_all, const Params<T>& P, const uint8_t* __r
                 const long long m = js < 0 ? (long long)L::opp(i) * N + nd.slot : (long long)i * N + js;
 #pragma unroll
                 for (int k = 0; k < K; ++k)
-                    f[k][i] = load_pop<L, T, S>(fs, (long long)k * L::Q * N + m, i, P.rho_ref[k0 + k]);
+                    f[k][i] = ld((long long)k * L::Q * N + m, i, k);
             }
             return;
         }
@@ -611,7 +645,7 @@ LBM_HD void gather_all(const void* f_all, const Params<T>& P, const uint8_t* __r
         if constexpr (!GEOM) {
 #pragma unroll
             for (int k = 0; k < K; ++k)
-                f[k][i] = load_pop<L, T, S>(fs, ((long long)k * L::Q + i) * N + src, i, P.rho_ref[k0 + k]);
+                f[k][i] = ld(((long long)k * L::Q + i) * N + src, i, k);
         } else {
             const unsigned face = i == 0 ? 0u : pull_face(g, L::ex(i), L::ey(i), L::ez(i));
             const bool unknown = (face & 2u) != 0u;   // constant-density x face (precedence)
@@ -631,7 +665,7 @@ LBM_HD void gather_all(const void* f_all, const Params<T>& P, const uint8_t* __r
             const long long m = bounce ? (long long)L::opp(i) * N + self : (long long)i * N + from;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                const T v = load_pop<L, T, S>(fs, (long long)k * L::Q * N + m, i, P.rho_ref[k0 + k]);
+                const T v = ld((long long)k * L::Q * N + m, i, k);
                 f[k][i] = unknown ? T(0) : v;
             }
         }
@@ -639,20 +673,20 @@ LBM_HD void gather_all(const void* f_all, const Params<T>& P, const uint8_t* __r
     if constexpr (GEOM) {
         if (P.bc[0] == BC_PRESSURE && nd.x == 0) {
 #pragma unroll
-            for (int k = 0; k < K; ++k) zou_he<L, T>(f[k], +1, P.bc_rho[0][k0 + k]);
+            for (int k = 0; k < K; ++k) zou_he<L, T>(f[k], +1, P.bc_rho[0][k0 + k], RAW ? P.rho_ref[k0 + k] : T(0));
         } else if (P.bc[1] == BC_PRESSURE && nd.x == P.nx - 1) {
 #pragma unroll
-            for (int k = 0; k < K; ++k) zou_he<L, T>(f[k], -1, P.bc_rho[1][k0 + k]);
+            for (int k = 0; k < K; ++k) zou_he<L, T>(f[k], -1, P.bc_rho[1][k0 + k], RAW ? P.rho_ref[k0 + k] : T(0));
         }
     }
 }
 
-template <class L, typename T, typename S, bool GEOM>
+template <class L, typename T, typename S, bool GEOM, bool DEV = false>
 LBM_HD void gather_k(const void* f_all, const Params<T>& P, const uint8_t* __restrict__ solid, const Node& nd,
                      int k, T (&f)[L::Q], const int* fidx = nullptr)
 {
     T fk[1][L::Q];
-    gather_all<L, T, S, 1, GEOM>(f_all, P, solid, fidx, nd, geo3<GEOM>(P, nd.x, nd.y, nd.z), fk, k);
+    gather_all<L, T, S, 1, GEOM, DEV>(f_all, P, solid, fidx, nd, geo3<GEOM>(P, nd.x, nd.y, nd.z), fk, k);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) f[i] = fk[0][i];
 }
@@ -1238,11 +1272,13 @@ __device__ __forceinline__ void density_node(const KArgs<T>& a, const Node& nd)
 {
     const long long N = a.p.N;
     bool bad = false, clamp = false;
+    // 16-bit storage: rho is the sum of the stored deviations plus rho_ref
+    constexpr bool DEV = pop_shifted<T, S>;
     T f[K][L::Q];
-    gather_all<L, T, S, K, GEOM>(a.f_src, a.p, a.solid, a.fidx, nd, geo3<GEOM>(a.p, nd.x, nd.y, nd.z), f);
+    gather_all<L, T, S, K, GEOM, DEV>(a.f_src, a.p, a.solid, a.fidx, nd, geo3<GEOM>(a.p, nd.x, nd.y, nd.z), f);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const T r = density<L, T>(f[k]);
+        const T r = DEV ? density<L, T>(f[k]) + a.p.rho_ref[k] : density<L, T>(f[k]);
         T ps, U;
         clamp |= pseudopotential<!pop_shifted<T, S>>(a.p, k, r, ps, U);
         a.psi[(long long)k * N + nd.n] = ps;
@@ -1456,10 +1492,13 @@ LBM_HD void psi_of_node(const KArgs<T>& a, int x, int y, int z, T (&out)[K])
     Node nd{x, y, z, (long long)x + (long long)a.p.nx * ((long long)y + (long long)a.p.ny * z)};
 #pragma unroll
     for (int k = 0; k < K; ++k) {
+        // 16-bit storage: rho from the stored deviations, as the density pass forms it
+        constexpr bool DEV = pop_shifted<T, S>;
         T f[L::Q];
-        gather_k<L, T, S, false>(a.f_src, a.p, nullptr, nd, k, f);
+        gather_k<L, T, S, false, DEV>(a.f_src, a.p, nullptr, nd, k, f);
         T U;
-        pseudopotential<!pop_shifted<T, S>>(a.p, k, density<L, T>(f), out[k], U);
+        const T r = DEV ? density<L, T>(f) + a.p.rho_ref[k] : density<L, T>(f);
+        pseudopotential<!pop_shifted<T, S>>(a.p, k, r, out[k], U);
     }
 }
 
