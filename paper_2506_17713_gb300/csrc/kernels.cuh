@@ -1303,18 +1303,33 @@ template <class L, typename T, int K>
 __device__ __forceinline__ void virtual_node(const KArgs<T>& a, int t)
 {
     const Params<T>& P = a.p;
-    const long long s = a.bsolid[t];
-    const int x = (int)(s % P.nx), y = (int)((s / P.nx) % P.ny), z = (int)(s / ((long long)P.nx * P.ny));
+    // node indices fit in 32 bits (the workspace of 2^31 nodes would exceed the HBM):
+    // the coordinates by the exact multiply-high division of the fluid-list kernels
+    const uint32_t s = (uint32_t)a.bsolid[t];
+    const uint32_t yz = fast_div(s, P.div_nx);
+    const uint32_t zq = fast_div(yz, P.div_ny);
+    const int x = (int)(s - yz * (uint32_t)P.nx), y = (int)(yz - zq * (uint32_t)P.ny), z = (int)zq;
     const long long N = P.N;
+    // the neighbours and their solid flags once for every component; each neighbour's
+    // density is loaded whatever the flag (the index is in range) and selected, so the
+    // loads do not wait on the flags. A solid neighbour adds an exact zero where it was
+    // skipped before, so the sums are unchanged bit for bit.
+    uint32_t m[L::Q];
+    uint32_t fl = 0u;   // bit i: neighbour i is fluid
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+        m[i] = (uint32_t)stencil_nb<true>(P, x, y, z, L::ex(i), L::ey(i), L::ez(i));
+        fl |= a.solid[m[i]] ? 0u : (1u << i);
+    }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         T num = T(0), den = T(0);
 #pragma unroll
         for (int i = 1; i < L::Q; ++i) {
-            const long long m = stencil_nb<true>(P, x, y, z, L::ex(i), L::ey(i), L::ez(i));
-            if (a.solid[m]) continue;
-            num += T(L::w(i)) * a.rho[(long long)k * N + m];
-            den += T(L::w(i));
+            const T r = a.rho[(long long)k * N + m[i]];
+            const bool f = (fl >> i) & 1u;
+            num += f ? T(L::w(i)) * r : T(0);
+            den += f ? T(L::w(i)) : T(0);
         }
         T r = P.wet_phi[k] * (num / den) - P.wet_drho[k];
         r = r < P.rho_min[k] ? P.rho_min[k] : r;
