@@ -295,8 +295,9 @@ void lbm_batch_destroy(lbm_batch* b);
  * that cannot allocate device memory at all -- processes where a framework owns every
  * allocation, or callers whose memory is used up by the lattice itself. It returns the
  * same sums as the mass part of lbm_diagnostics, from populations the caller already
- * holds. It copies its totals to host memory and synchronises the stream, so it cannot
- * be called on a stream that is being captured into a CUDA graph (the capture would fail).
+ * holds. It copies its totals to host memory and synchronises the stream, which a stream
+ * being captured into a CUDA graph cannot do: on such a stream it returns
+ * LBM_ERR_INVALID_ARG before enqueuing anything, and the capture stays valid.
  *
  *   p     lattice parameters; lattice, nx, ny, nz, ncomp and real are used.
  *   d_f   device pointer, post-stream populations [ncomp][Q][N] of the real type of p,

@@ -1295,9 +1295,9 @@ __device__ __forceinline__ void virtual_node(const KArgs<T>& a, int t)
     const int x = (int)(s - yz * (uint32_t)P.nx), y = (int)(yz - zq * (uint32_t)P.ny), z = (int)zq;
     const long long N = P.N;
     // the neighbours and their solid flags once for every component; each neighbour's
-    // density is loaded whatever the flag (the index is in range) and selected, so the
-    // loads do not wait on the flags. A solid neighbour adds an exact zero where it was
-    // skipped before, so the sums are unchanged bit for bit.
+    // density is loaded whatever the flag (the index is in range), and the flag selects
+    // whether the sums take it, so the loads do not wait on the flags. A fluid neighbour
+    // is taken as one fused multiply-add, num = fma(w, rho, num).
     // (the per-node offset table of the force stencil: periodic faces wrap, other faces
     // clamp, two adds per neighbour)
     const Geo3 g = geo3<true>(P, x, y, z);
@@ -1315,8 +1315,8 @@ __device__ __forceinline__ void virtual_node(const KArgs<T>& a, int t)
         for (int i = 1; i < L::Q; ++i) {
             const T r = a.rho[(long long)k * N + m[i]];
             const bool f = (fl >> i) & 1u;
-            num += f ? T(L::w(i)) * r : T(0);
-            den += f ? T(L::w(i)) : T(0);
+            num = f ? fma(T(L::w(i)), r, num) : num;
+            den = f ? den + T(L::w(i)) : den;
         }
         T r = P.wet_phi[k] * (num / den) - P.wet_drho[k];
         r = r < P.rho_min[k] ? P.rho_min[k] : r;

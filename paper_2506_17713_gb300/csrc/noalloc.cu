@@ -7,7 +7,8 @@
 // partial sums of the two-stage reduction) in a file-scope device array instead of a
 // caller workspace. That array lives on every GPU that loads the library until the
 // process exits. The call copies the totals to host memory and synchronises its
-// stream, so it cannot run on a stream that is being captured into a CUDA graph.
+// stream, which a stream being captured into a CUDA graph cannot do: on such a stream
+// it returns LBM_ERR_INVALID_ARG before enqueuing anything, so the capture stays valid.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -110,10 +111,15 @@ extern "C" lbm_status lbm_mass_noalloc(const lbm_params* p, const void* d_f, dou
     const long long N = (long long)p->nx * p->ny * p->nz;
     if (N > LBM_NOALLOC_MAX_NODES) return LBM_ERR_INVALID_ARG;  // scratch holds this many nodes
     const int Q = p->lattice == LBM_D2Q9 ? 9 : 19;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the copy to host memory and the synchronisation below are not allowed on a stream
+    // that is being captured: refuse it before anything is enqueued
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return LBM_ERR_CUDA;
+    if (cs != cudaStreamCaptureStatusNone) return LBM_ERR_INVALID_ARG;
     double* scratch = nullptr;
     const lbm_status s = scratch_of_current_device(&scratch);
     if (s != LBM_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
     const int nblocks = (int)((N + kNodesPerBlock - 1) / kNodesPerBlock);
     if (p->real == LBM_FP64)
         k_mass_partials<double><<<nblocks, kThreads, 0, st>>>((const double*)d_f, p->ncomp, Q, N, scratch);

@@ -2,8 +2,9 @@
 
 It must give the mass that lbm_diagnostics gives for the same lattice, on two calls
 in a row (the second reuses the scratch the first left behind), and it must refuse
-lattices larger than its fixed scratch covers. This file is collected last on
-purpose.
+lattices larger than its fixed scratch covers, 16-bit storage, and a stream that is
+being captured into a CUDA graph (without breaking the capture). This file is
+collected last on purpose.
 """
 import ctypes as C
 
@@ -80,3 +81,30 @@ def test_mass_noalloc_rejects_16bit_storage():
         p = lbm.params_from_case(cases.base_case("D3Q19", (16, 16, 16), real=real))
         mass = (C.c_double * 2)()
         assert lbm.library().lbm_mass_noalloc(C.byref(p), C.c_void_p(256), mass, None) == 1
+
+
+def test_mass_noalloc_refuses_a_capturing_stream():
+    # the call ends in a copy to host memory and a stream synchronisation, which capture
+    # does not allow: it must return LBM_ERR_INVALID_ARG before enqueuing anything, so the
+    # caller's capture completes and replays; outside the capture the same call works
+    import torch
+    from paper_2506_17713_gb300 import lbm
+    lat = _lattice("pr_f32")
+    mass_ref, _ = lat.diagnostics()
+    f = torch.stack([lat.populations(k) for k in range(lat.K)]).contiguous()
+    x = torch.zeros(4, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    mass = (C.c_double * 2)()
+    with torch.cuda.graph(g, stream=side):
+        x.add_(1.0)
+        st = torch.cuda.current_stream().cuda_stream
+        code = lbm.library().lbm_mass_noalloc(C.byref(lat.params), C.c_void_p(f.data_ptr()), mass, C.c_void_p(st))
+        x.add_(1.0)
+    assert code == 1      # LBM_ERR_INVALID_ARG
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(x, torch.full_like(x, 2.0))
+    m = lbm.lbm_mass_noalloc(lat.params, f.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert np.allclose(m, mass_ref, rtol=6e-8, atol=0.0)
+    lat.close()
