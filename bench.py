@@ -134,10 +134,16 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def committed_traffic(kernel, workload, n):
+# compute and storage types in a step kernel's template arguments, per population storage
+KERNEL_TYPES = {"f32": "float, float", "f64": "double, double", "f16s": "float, __half",
+                "bf16s": "float, __nv_bfloat16"}
+
+
+def committed_traffic(kernel, workload, n, real="f32"):
     """DRAM bytes per launch of `kernel` (dram__bytes_read.sum + dram__bytes_write.sum)
-    from the committed ncu summary of this workload, or None when there is none or the
-    kernel sources have changed since it was captured."""
+    from the committed ncu summary of this workload, for the instantiation of this
+    population storage, or None when there is none or the kernel sources have changed
+    since it was captured."""
     path = os.path.join(ROOT, "profiles", "dram_traffic_%s_n%d.md" % (workload, n))
     if not os.path.exists(path):
         return None
@@ -147,7 +153,8 @@ def committed_traffic(kernel, workload, n):
             if line.startswith("kernel sources sha256:"):
                 digest = line.split(":", 1)[1].strip()
             cells = [c.strip() for c in line.strip().strip("|").split("|")]
-            if len(cells) >= 5 and cells[0].startswith(kernel + "<"):
+            if len(cells) >= 5 and cells[0].startswith(kernel + "<") and \
+                    (", %s," % KERNEL_TYPES[real]) in cells[0]:
                 try:
                     value = int(cells[4])
                 except ValueError:
@@ -838,7 +845,8 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": "k_fused" if fused else "k_collide", "achieved": round(ach_col, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(ach_col / peak, 4),
                      "peak_kind": peak_kind,
-                     "traffic": committed_traffic("k_fused" if fused else "k_collide", args.workload, args.n),
+                     "traffic": committed_traffic("k_fused" if fused else "k_collide", args.workload, args.n,
+                                                  case.get("real", "f32")),
                      "bytes_per_lu": abytes["collide"], "units_per_launch": units,
                      "ms_per_launch": round(t_col * 1e3, 4),
                      "density_kernel": {"achieved": round(ach_den, 1), "frac": round(ach_den / peak, 4),

@@ -77,6 +77,9 @@ def test_committed_traffic_is_gated_by_kernel_source_hash(monkeypatch):
     t = bench.committed_traffic("k_collide", "pr256", 256)
     assert isinstance(t, int) and t > 0
     assert bench.committed_traffic("k_collide", "pr256", 128) is None      # no summary for that size
+    # the FP32 instantiation's bytes are not those of the 16-bit storage kernels
+    assert bench.committed_traffic("k_collide", "pr256", 256, "f16s") is None
+    assert bench.committed_traffic("k_collide", "pr256", 256, "bf16s") is None
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 64)
     assert bench.committed_traffic("k_collide", "pr256", 256) is None      # kernels changed since the capture
 
