@@ -6,7 +6,8 @@ flat-interface coexistence against the Maxwell construction (Section 3.1, D2Q9 a
 D3Q19), Laplace's law (Section 3.2; 2-D, and 3-D with Delta p = 2 sigma / R), wetting
 (Section 2.4): the contact-angle measurement on a mirror wall, neutral phi = 1 near 90
 degrees (Section 3.3.2), the monotone effect of phi / drho, and the calibrated phi of the
-workloads reproducing their set angles.
+workloads reproducing their set angles; the D3Q19 MRT collision with two-relaxation-time
+rates reaching the BGK steady state of a porous sample scaled by the viscosity ratio.
 """
 import numpy as np
 import pytest
@@ -287,3 +288,44 @@ def test_cocurrent_two_layer_channel_against_closed_form():
     qn = 2 * trap(np.where(yy <= b, uu, 0.0), yy)
     assert abs(qw / (q0 / mu_w) - 0.5 * Sw ** 2 * (3 - Sw)) < 1e-6
     assert abs(qn / (q0 / mu_nw) - (1 - Sw) * (1.5 * M + (1 - Sw) ** 2 * (1 - 1.5 * M))) < 1e-6
+
+
+def _porous_flow(collision, tau, rates=None, n=16, steps=8000):
+    from synth import grf_porous_medium
+    solid, _ = grf_porous_medium((n, n, n), 0.25, 3.0, 1001, buffer=0, periodic_x=True)
+    case = cases.base_case("D3Q19", (n, n, n), collision=collision, psi=["rho", "rho"], g=[[0.0, 0.0], [0.0, 0.0]],
+                           tau=[tau, tau], accel=[[1e-5, 0.0, 0.0], [0.0, 0.0, 0.0]], real="f64")
+    if rates is not None:
+        case["mrt_rates"] = [rates, rates]
+    s = oracle.OracleSim(case)
+    s.set_geometry(solid)
+    s.init_fields(0, np.ones((n, n, n)))
+    s.step(steps)
+    _, u = s.macroscopic(0)
+    return u, solid == 0
+
+
+def test_trt_rates_reach_the_bgk_steady_state_scaled_by_viscosity():
+    # Section 2.1 (Eq. collision_model, MRT). With even non-conserved moments (energy, its
+    # square, stresses, their fourth-order companions) relaxed at 1/tau+ and odd ones
+    # (energy fluxes, third-order moments) at 1/tau-, the collision is the two-relaxation-
+    # time scheme; with halfway bounce-back its creeping-flow steady states depend on the
+    # viscosity only through u ~ a / nu while (tau+ - 1/2)(tau- - 1/2) is held. BGK at tau = 1
+    # is the case tau+ = tau- = 1, magic number 1/4. So MRT at tau+ = 2, tau- = 1/2 + 1/6,
+    # scaled by nu'/nu = 3, must give the BGK tau = 1 velocity of a porous sample (up to the
+    # small inertial and forcing terms); BGK itself at tau = 2 (a different magic number)
+    # must not. A rate sent to the wrong moment breaks the first.
+    ub, fl = _porous_flow("BGK", 1.0)
+    sp, sm = 1.0 / 2.0, 1.0 / (0.5 + 0.25 / 1.5)
+    rates = [0.0, sp, sp, 0.0, sm, 0.0, sm, 0.0, sm, sp, sp, sp, sp, sp, sp, sp, sm, sm, sm]
+    ut, _ = _porous_flow("MRT", 2.0, rates)
+    u2, _ = _porous_flow("BGK", 2.0)
+    scale = (2.0 - 0.5) / (1.0 - 0.5)
+    umax = np.abs(ub[:, fl]).max()
+    err = np.abs(scale * ut - ub)[:, fl].max() / umax
+    flux = scale * ut[0][fl].mean() / ub[0][fl].mean()
+    flux_bgk2 = scale * u2[0][fl].mean() / ub[0][fl].mean()
+    print("TRT tau+ = 2: max |du| / max|u| %.2e, flux ratio %.7f; BGK tau = 2: flux ratio %.4f" % (err, flux, flux_bgk2))
+    assert err < 2e-3
+    assert abs(flux - 1.0) < 1e-4
+    assert abs(flux_bgk2 - 1.0) > 0.1
