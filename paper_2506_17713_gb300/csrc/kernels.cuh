@@ -1294,12 +1294,13 @@ __device__ __forceinline__ void virtual_node(const KArgs<T>& a, int t)
     const uint32_t zq = fast_div(yz, P.div_ny);
     const int x = (int)(s - yz * (uint32_t)P.nx), y = (int)(yz - zq * (uint32_t)P.ny), z = (int)zq;
     const long long N = P.N;
-    // the neighbours and their solid flags once for every component; each neighbour's
-    // density is loaded whatever the flag (the index is in range), and the flag selects
-    // whether the sums take it, so the loads do not wait on the flags. A fluid neighbour
-    // is taken as one fused multiply-add, num = fma(w, rho, num).
-    // (the per-node offset table of the force stencil: periodic faces wrap, other faces
-    // clamp, two adds per neighbour)
+    // The neighbours come from the per-node offset table of the force stencil (periodic
+    // faces wrap, other faces clamp; two adds per neighbour), with their solid flags, once
+    // for every component. Each neighbour's density is then loaded whatever its flag (the
+    // index is in range) and the flag selects whether the sums take it, so the loads do
+    // not wait on the flags. A solid neighbour's value -- which this pass may be writing at
+    // the same time, if that solid is a boundary solid too -- is never used. A fluid
+    // neighbour is taken as one fused multiply-add, num = fma(w, rho, num).
     const Geo3 g = geo3<true>(P, x, y, z);
     uint32_t m[L::Q];
     uint32_t fl = 0u;   // bit i: neighbour i is fluid
