@@ -312,6 +312,39 @@ def test_rest_state_stays_at_rest():
     assert np.allclose(s.populations(0), f0, atol=1e-15)
 
 
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19"])
+def test_equilibrium_moments_of_a_moving_state(lattice):
+    # Section 2.1 (the equilibrium of Eq. collision_model): f^eq(rho, u) has density rho,
+    # momentum rho u and momentum flux rho (c_s^2 I + u u) exactly; the last one is what the
+    # 4.5 (e.u)^2 and -1.5 u.u terms are for, and a flow as slow as Poiseuille's cannot see
+    # them. The populations the oracle starts from a uniform moving state (density 1.3, u of
+    # order 0.1) are checked against the three moments, with the velocity set compared to
+    # the textbook one; with no density gradient there is no force, so the state is also a
+    # fixed point of the step.
+    shape = (5, 4, 3) if lattice == "D3Q19" else (5, 4, 1)
+    D = 3 if lattice == "D3Q19" else 2
+    case = cases.base_case(lattice, shape, collision="MRT")
+    case = cases.with_eos(case, "PR", 0.6)
+    s = oracle.OracleSim(case)
+    e = np.asarray(s.e, dtype=np.int64)[:, :D]
+    want = {tuple(v) for v in np.ndindex(*(3,) * D)}
+    want = {tuple(c - 1 for c in v) for v in want if (D == 2 or sum(abs(c - 1) for c in v) <= 2)}
+    assert {tuple(v) for v in e} == want and len(e) == len(want)
+    U = np.array([0.11, -0.07, 0.05])[:D]
+    rho = 1.3
+    u = np.broadcast_to(U.reshape((D,) + (1,) * 3), (D,) + s.shape).copy()
+    s.init_fields(0, np.full(s.shape, rho), u)
+    f = s.populations(0).reshape(len(e), -1)[:, 0]
+    cs2 = 1.0 / 3.0
+    assert abs(f.sum() - rho) < 1e-14
+    assert np.allclose(e.T @ f, rho * U, atol=1e-15, rtol=0)
+    flux = np.einsum("ia,ib,i->ab", e, e, f)
+    assert np.allclose(flux, rho * (cs2 * np.eye(D) + np.outer(U, U)), atol=1e-14, rtol=0)
+    f0 = s.populations(0)
+    s.step(3)
+    assert np.allclose(s.populations(0), f0, atol=1e-14, rtol=0)
+
+
 # ---------------------------------------------------------------------------
 # Wetting (Eq. improved_virtual_density)
 # ---------------------------------------------------------------------------
