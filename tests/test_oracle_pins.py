@@ -431,6 +431,31 @@ def test_neutral_wetting_flat_wall_force_vanishes_normal():
 # Constant-density faces
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19"])
+def test_pressure_faces_pass_a_uniform_normal_flow(lattice):
+    # Section 3.4.3's constant-density faces (the paper names no scheme; the reading is the
+    # Zou-He closure):
+    # for the equilibrium of a uniform flow normal to the faces at the face density, the
+    # closure's rho u_n = rho_b - (sum_{e_x = 0} f + 2 sum_{e_x < 0} f) returns rho U_x
+    # exactly and f_i - f_opp(i) = 6 w_i rho U_x, so the state passes through both faces
+    # and stays a fixed point of the step; a sign or weight error in the closure breaks it
+    D = 3 if lattice == "D3Q19" else 2
+    shape = (9, 4, 3) if D == 3 else (9, 4, 1)
+    rho, U = 1.1, 0.04
+    case = cases.base_case(lattice, shape, psi=["rho"], g=[[0.0, 0.0], [0.0, 0.0]],
+                           bc=["pressure", "pressure"] + ["periodic"] * 4,
+                           bc_rho=[[rho, 0], [rho, 0]] + [[0, 0]] * 4)
+    s = oracle.OracleSim(case)
+    u = np.zeros((D,) + s.shape)
+    u[0] = U
+    s.init_fields(0, np.full(s.shape, rho), u)
+    f0 = s.populations(0)
+    s.step(5)
+    assert np.allclose(s.populations(0), f0, atol=1e-14, rtol=0)
+    r, uo = s.macroscopic(0)
+    assert np.allclose(r, rho, atol=1e-14) and np.allclose(uo[0], U, atol=1e-14)
+
+
 def test_pressure_faces_fix_density_and_tangential_momentum():
     shape = (12, 7, 6)
     case = cases.base_case("D3Q19", shape, psi=["rho"], g=[[0.0, 0.0], [0.0, 0.0]],
