@@ -200,6 +200,31 @@ def test_two_component_per_component_velocity_bgk_fp64():
     compare(lat, orc, TOL64)
 
 
+@pytest.mark.parametrize("lattice,real", [("D2Q9", "f64"), ("D3Q19", "f64"), ("D3Q19", "f32")])
+def test_pressure_faces_pass_a_uniform_normal_flow(lattice, real):
+    # Section 3.4.3 (constant-density faces, read as the Zou-He closure): the equilibrium of
+    # a uniform flow along x at the face density is a fixed point of the step through both
+    # faces; on the GPU to the rounding of the storage type, and equal to the oracle
+    from paper_2506_17713_gb300 import Lattice
+    D = 3 if lattice == "D3Q19" else 2
+    shape = (9, 4, 3) if D == 3 else (9, 4, 1)
+    rho, U = 1.1, 0.04
+    case = cases.base_case(lattice, shape, psi=["rho"], g=[[0.0, 0.0], [0.0, 0.0]], real=real,
+                           bc=["pressure", "pressure"] + ["periodic"] * 4,
+                           bc_rho=[[rho, 0], [rho, 0]] + [[0, 0]] * 4)
+    u0 = np.zeros((D,) + tuple(reversed(shape)))
+    u0[0] = U
+    lat = Lattice(case)
+    lat.init_fields(0, np.full(tuple(reversed(shape)), rho), u0)
+    lat.step(5)
+    r, u = lat.macroscopic_host(0)
+    tol = 1e-13 if real == "f64" else 1e-6
+    assert np.abs(r.astype(np.float64) - rho).max() <= tol * rho
+    assert np.abs(u[0].astype(np.float64) - U).max() <= tol
+    assert np.abs(u[1:].astype(np.float64)).max() <= tol
+    lat.close()
+
+
 def test_pressure_faces_two_component_porous():
     shape = (40, 18, 16)
     case, init = cases.porous_two_component(shape=shape, porosity=0.6, corr_length=3.0, buffer=4)
