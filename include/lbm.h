@@ -108,7 +108,8 @@ enum { LBM_SCHEDULE_AUTO = 0, LBM_SCHEDULE_TWO_PASS = 1, LBM_SCHEDULE_SINGLE_PAS
  *   wet_phi, wet_drho virtual solid density rho_s = wet_phi * rho_ave - wet_drho
  *                     (phi >= 1 with drho = 0 for theta <= 90 deg, phi = 1 with drho >= 0
  *                     above), limited to [rho_min, rho_max].
- *   body_accel[k][d]  body acceleration a^k: the body force is rho^k a^k.
+ *   body_accel[k][d]  body acceleration a^k: the body force is rho^k a^k. On D2Q9 the z
+ *                     component must be 0 (LBM_ERR_INVALID_ARG otherwise).
  *   bc[f]             face kinds, faces -x,+x,-y,+y,-z,+z (z faces ignored in 2-D).
  *   bc_rho[f][k]      densities of constant-density faces.
  *

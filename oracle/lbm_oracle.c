@@ -548,6 +548,8 @@ orc_sim* orc_create(const orc_params* p)
     if (!p || (p->dim != 2 && p->dim != 3) || p->ncomp < 1 || p->ncomp > 2) return NULL;
     if (p->nx < 1 || p->ny < 1 || p->nz < 1 || (p->dim == 2 && p->nz != 1)) return NULL;
     if (p->forcing != ORC_FORCE_EDM && p->forcing != ORC_FORCE_MOMENT) return NULL;
+    /* a 2-D lattice has no z velocity: a z acceleration is refused, not carried in u.u */
+    if (p->dim == 2 && (p->accel[0][2] != 0.0 || p->accel[1][2] != 0.0)) return NULL;
     orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
     s->p = *p;
     s->dims[0] = p->nx; s->dims[1] = p->ny; s->dims[2] = p->nz;

@@ -201,6 +201,8 @@ lbm_status validate(const lbm_params* p)
             return LBM_ERR_INVALID_ARG;
         for (int d = 0; d < 3; ++d)
             if (!fin(p->body_accel[k][d])) return LBM_ERR_INVALID_ARG;
+        // a 2-D lattice has no z velocity: a z acceleration would only enter u.u
+        if (p->lattice == LBM_D2Q9 && p->body_accel[k][2] != 0.0) return LBM_ERR_INVALID_ARG;
         for (int f = 0; f < 2; ++f)
             if (p->bc[f] == LBM_BC_PRESSURE && !(p->bc_rho[f][k] > 0)) return LBM_ERR_INVALID_ARG;
     }

@@ -104,6 +104,7 @@ def test_workspace_size_layout(lib):
     dict(real="f16s", rho_ref=[float("nan"), 1.0]),
     dict(kappa=[0.5, 0.5]),                    # surface-tension source: D2Q9 MRT only
     dict(forcing="moment"),                    # moment-space forcing: D2Q9 only
+    dict(lattice="D2Q9", shape=(16, 12, 1), accel=[[0.0, 0.0, 1e-5], [0.0, 0.0, 0.0]]),  # no z in 2-D
 ])
 def test_rejects_invalid_parameters(lib, bad):
     from paper_2506_17713_gb300 import lbm

@@ -431,6 +431,17 @@ def test_neutral_wetting_flat_wall_force_vanishes_normal():
 # Constant-density faces
 # ---------------------------------------------------------------------------
 
+def test_two_dimensional_lattice_refuses_a_z_acceleration():
+    # D2Q9 has no z velocity; a z acceleration would only have entered u.u of the shifted
+    # equilibrium, so the oracle refuses it (as the C ABI does)
+    case = cases.base_case("D2Q9", (8, 6, 1), psi=["rho"], g=[[0.0, 0.0], [0.0, 0.0]],
+                           accel=[[1e-5, 0.0, 1e-5], [0.0, 0.0, 0.0]])
+    with pytest.raises(ValueError):
+        oracle.OracleSim(case)
+    case["accel"] = [[1e-5, 0.0, 0.0], [0.0, 0.0, 0.0]]
+    oracle.OracleSim(case)
+
+
 @pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19"])
 def test_pressure_faces_pass_a_uniform_normal_flow(lattice):
     # Section 3.4.3's constant-density faces (the paper names no scheme; the reading is the
