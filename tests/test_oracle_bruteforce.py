@@ -264,3 +264,20 @@ def test_headline_workload_step_against_brute_force():
     rel = _compare(case, [random_field(shape, rg, rl, 76)], p)
     print("D3Q19 MRT Peng-Robinson (headline configuration), 4 steps: max rel %.2e" % rel)
     assert rel < 1e-13
+
+
+def test_two_components_with_self_coupling_and_mixing_against_brute_force():
+    # the general two-component force: self couplings g_kk != 0 with mixing weights A_k (the
+    # Zhang-Chen term on U_k = g_kk psi_k^2 / 2) and the cross coupling, psi = exp(-1/rho),
+    # each component at its own velocity and tau, a body force on one component
+    shape = (4, 3, 5)
+    g = [[-1.2, 0.4], [0.4, -1.0]]
+    A = [0.3, 0.1]
+    tau = [0.9, 1.2]
+    accel = [[5e-5, 0.0, -1e-4], [0.0, 0.0, 0.0]]
+    case = cases.base_case("D3Q19", shape, ncomp=2, psi=["exp", "exp"], g=g, A=A, velocity="component",
+                           collision="BGK", tau=tau, accel=accel, real="f64")
+    p = dict(psi="exp", g=g, A=A, tau=tau, accel=accel)
+    rel = _compare(case, [random_field(shape, 0.5, 1.3, 77), random_field(shape, 0.4, 1.1, 78)], p)
+    print("D3Q19 two components, self coupling and mixing, 4 steps: max rel %.2e" % rel)
+    assert rel < 1e-13
