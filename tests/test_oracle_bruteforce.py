@@ -281,3 +281,87 @@ def test_two_components_with_self_coupling_and_mixing_against_brute_force():
     rel = _compare(case, [random_field(shape, 0.5, 1.3, 77), random_field(shape, 0.4, 1.1, 78)], p)
     print("D3Q19 two components, self coupling and mixing, 4 steps: max rel %.2e" % rel)
     assert rel < 1e-13
+
+
+def _mrt_d2q9(e):
+    # Lallemand and Luo's D2Q9 moments: rho, e, eps, jx, qx, jy, qy, pxx, pxy
+    x, y = (e[:, d].astype(float) for d in range(2))
+    c2 = x * x + y * y
+    return np.array([np.ones_like(x), -4 + 3 * c2, 4 - 10.5 * c2 + 4.5 * c2 * c2, x, (-5 + 3 * c2) * x,
+                     y, (-5 + 3 * c2) * y, x * x - y * y, x * y])
+
+
+def _step_kappa(f, e, w, p):
+    # Section 2.3 with the reading the oracle states: f* = f - M^-1 [S (m - m^eq(v)) - C - F_m],
+    # v = (sum f e + F / 2) / rho, F_m = (I - S / 2) M S_G with Guo's source
+    # S_G,i = w_i [3 (e_i - v) + 9 (e_i . v) e_i] . F, and C of Eq. li_surface_adjust in the
+    # e, eps, pxx, pxy moments from Q = kappa g / 2 [(1 - A) psi sum_i G_i (psi_i - psi) e_i e_i
+    # + A / 2 sum_i G_i (psi_i^2 - psi^2) e_i e_i]; one component, psi = exp(-1/rho)
+    g, A, kap, tau = p["g"], p["A"], p["kappa"], p["tau"]
+    G = w / CS2
+    fk = f[0]
+    rho = fk.sum(axis=0)
+    j = np.einsum("id,i...->d...", e, fk)
+    psi = np.exp(-1.0 / rho)
+    U = 0.5 * g * psi * psi
+    F = np.zeros((2,) + rho.shape)
+    Qxx, Qyy, Qxy = (np.zeros_like(rho) for _ in range(3))
+    for i in range(len(e)):
+        if not e[i].any():
+            continue
+        pn = _shift(psi, e[i])
+        ev = e[i].reshape(2, 1, 1)
+        F += A * (-G[i] * _shift(U, e[i]) * ev) + (1 - A) * (-psi * g * G[i] * pn * ev)
+        t = G[i] * ((1 - A) * psi * (pn - psi) + 0.5 * A * (pn * pn - psi * psi))
+        Qxx += t * e[i][0] ** 2
+        Qyy += t * e[i][1] ** 2
+        Qxy += t * e[i][0] * e[i][1]
+    F += rho * np.asarray(p["accel"][:2]).reshape(2, 1, 1)
+    kg = 0.5 * kap * g
+    Qxx, Qyy, Qxy = kg * Qxx, kg * Qyy, kg * Qxy
+    rates = np.array(p["rates"], dtype=float)[:9]
+    rates[[7, 8]] = 1.0 / tau
+    rates[[0, 3, 5]] = 0.0
+    M = _mrt_d2q9(e)
+    Mi = np.linalg.inv(M)
+    v = (j + 0.5 * F) / rho
+    m = np.einsum("ai,i...->a...", M, fk)
+    meq = np.einsum("ai,i...->a...", M, _feq(e, w, rho, v))
+    ev = np.einsum("id,d...->i...", e, v)
+    eF = np.einsum("id,d...->i...", e, F)
+    vF = (v * F).sum(axis=0)
+    SG = w.reshape(-1, 1, 1) * (3 * (eF - vF) + 9 * ev * eF)
+    Fm = np.einsum("ai,i...->a...", M, SG) * (1 - 0.5 * rates).reshape(-1, 1, 1)
+    C = np.zeros_like(m)
+    C[1] = 1.5 * rates[1] * (Qxx + Qyy)
+    C[2] = -1.5 * rates[2] * (Qxx + Qyy)
+    C[7] = -rates[7] * (Qxx - Qyy)
+    C[8] = -rates[8] * Qxy
+    ms = m - rates.reshape(-1, 1, 1) * (m - meq) + C + Fm
+    fs = np.einsum("ia,a...->i...", Mi, ms)
+    return [np.stack([_shift(fs[i], -e[i]) for i in range(len(e))])]
+
+
+@pytest.mark.parametrize("kappa", [0.0, 0.5])
+def test_surface_tension_adjustment_step_against_brute_force(kappa):
+    # D2Q9 MRT with the moment-space forcing of Eq. mrt_surface and the source C of Eq.
+    # li_surface_adjust (kappa = 0.5; kappa = 0 checks the forcing alone), psi = exp(-1/rho),
+    # g = -1.5, A = -0.4, tau = 1, a body force
+    shape = (7, 6, 1)
+    g, A, tau = -1.5, -0.4, 1.0
+    accel = [[2e-5, -1e-5, 0.0], [0.0, 0.0, 0.0]]
+    case = cases.base_case("D2Q9", shape, collision="MRT", psi=["exp", "exp"], g=[[g, 0.0], [0.0, g]], A=[A, A],
+                           tau=[tau, tau], kappa=[kappa, kappa], forcing="moment", accel=accel, real="f64")
+    p = dict(g=g, A=A, kappa=kappa, tau=tau, accel=accel[0], rates=case["mrt_rates"][0])
+    s = oracle.OracleSim(case)
+    s.init_fields(0, random_field(shape, 0.6, 1.4, 79))
+    e = np.asarray(s.e, dtype=np.int64)[:, :2]
+    _check_set(e)
+    w = _weights(e)
+    f = [s.populations(0)[:, 0]]
+    for _ in range(4):
+        f = _step_kappa(f, e, w, p)
+    s.step(4)
+    rel = np.abs(s.populations(0)[:, 0] - f[0]).max() / np.abs(f[0]).max()
+    print("D2Q9 MRT, moment-space forcing, kappa = %.1f, 4 steps: max rel %.2e" % (kappa, rel))
+    assert rel < 1e-13
